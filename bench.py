@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark of the two-component LBM step on GB300 (D3Q19 CG and SC oscillating droplet).
+
+Workload (one "step"): one colour-gradient timestep of a 128^3 D3Q19 lattice (ellipsoidal
+droplet, semi-axes 24/20/20, density ratio 10, A = 5e-3, tau = 1, +-1% seeded noise) and one
+Shan-Chen multiphase timestep of a 128^3 D3Q19 lattice (same ellipsoid, G = -5, rho_0 = 1),
+both FP32.  value = lattice updates of both lattices per second (MLUPS); both lattices'
+populations (318 MB + 159 MB) exceed the 126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own pair of lattices (independent replicas, weak
+scaling); rank 0 prints one JSON line with the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2110_05197_gb300 import inputs  # noqa: E402
+
+METRIC = "CG/SC D3Q19 MLUPS & % HBM roofline; sweep sims/hr + p99 latency vs plain"
+N3 = 128
+SEMI = (24.0, 20.0, 20.0)
+SC_LIQ, SC_GAS = 1.8884, 0.1194          # SC coexistence at G = -5 (mechanical stability)
+BYTES_PER_LU = {"cg": 2 * 2 * 19 * 4, "sc": 2 * 1 * 19 * 4}   # FP32 read + write of all populations
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_fields(n=N3, nz=None):
+    nz = nz or n
+    ins = inputs.ellipsoid(n, n, nz, SEMI, centre=((n - 1) / 2, (n - 1) / 2, (nz - 1) / 2))
+    rr, rb = inputs.two_fluid(ins, 1.0, 0.1, 0.01, 2)
+    rho_sc = np.where(ins, SC_LIQ, SC_GAS) * (1 + 0.01 * inputs.uniform_pm1(2, ins.size))
+    return rr, rb, rho_sc
+
+
+def cg_kw(n=N3, nz=None):
+    return dict(lattice=1, model=0, nx=n, ny=n, nz=nz or n, rho_r0=1.0, rho_b0=0.1, alpha_b=0.2,
+                tau_r=1.0, tau_b=1.0, A=5e-3, beta=0.7)
+
+
+def sc_kw(n=N3, nz=None):
+    return dict(lattice=1, model=1, nx=n, ny=n, nz=nz or n, G=-5.0, rho0_psi=1.0, tau_r=1.0)
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample_mlups(steps: int, nz: int = 16, threads: int | None = None):
+    """FP64 CPU oracle on a 128 x 128 x nz slab of the same droplet workload (CG + SC)."""
+    import oracle
+    oracle.build()
+    threads = threads or os.cpu_count() or 1
+    oracle.set_threads(threads)
+    rr, rb, rho = workload_fields(N3, nz)
+    cg = oracle.OracleSim(oracle.Params(**cg_kw(N3, nz))).init(rr, rb)
+    sc = oracle.OracleSim(oracle.Params(**sc_kw(N3, nz))).init(rho)
+    n = N3 * N3 * nz
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        cg.step(1)
+        sc.step(1)
+    dt = time.perf_counter() - t0
+    return 2 * n * steps / dt / 1e6, oracle.get_threads(), dt, n
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    nz = 8
+    mlups_w, cores, _, n = oracle_sample_mlups(max(1, args.warmup), nz)
+    mlups, cores, dt, n = oracle_sample_mlups(args.steps, nz)
+    sample = f"128x128x{nz} slab of the 128^3 droplet workload, CG + SC FP64 oracle, {args.steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "D3Q19 CG+SC oscillating droplet (oracle sample)",
+                                            "nodes_per_lattice": n},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2110_05197_gb300 import build, lbm
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    rr, rb, rho = workload_fields()
+    n = N3 ** 3
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    cg = lbm.Lattice(lbm.Params(precision=lbm.FP32, **cg_kw()))
+    sc = lbm.Lattice(lbm.Params(precision=lbm.FP32, **sc_kw()))
+    cg.init(t(rr), t(rb))
+    sc.init(t(rho))
+    if args.profile_only:
+        lat = cg if args.profile_only == "cg" else sc
+        lat.step(args.warmup + args.steps)
+        torch.cuda.synchronize()
+        return 0
+    for _ in range(args.warmup):
+        cg.step(1)
+        sc.step(1)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = cg.launch_count() + sc.launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        start.record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            cg.step(1)
+            ev[k][1].record(stream)
+            sc.step(1)
+            ev[k][2].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+    launches = cg.launch_count() + sc.launch_count() - l0
+    total_ms = start.elapsed_time(end)
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    cg_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    sc_ms = [b.elapsed_time(c) for _, b, c in ev]
+    cg_avg, sc_avg = float(np.mean(cg_ms)), float(np.mean(sc_ms))
+    value = 2 * n * K * ws / (total_ms / 1e3) / 1e6
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_LU["cg"] * n / (cg_avg / 1e3) / 1e9
+    tot_cg, rc_cg = cg.totals()
+    tot_sc, rc_sc = sc.totals()
+
+    # end to end through the public API with pinned host buffers: init from host fields,
+    # K CG + K SC steps, densities and totals back to the host
+    pin = lambda a: torch.as_tensor(a, dtype=torch.float64).pin_memory()
+    h_rr, h_rb, h_rho = pin(rr), pin(rb), pin(rho)
+    o_rr, o_rb, o_sc = (torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3))
+    totals = np.zeros(lbm.NTOTALS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cg.init(h_rr, h_rb)
+    sc.init(h_rho)
+    cg.step(K)
+    sc.step(K)
+    cg.moments_into(o_rr, o_rb, None, None, totals)
+    sc.moments_into(o_sc, None, None, None, totals)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = 3 * n * 8
+    d2h = 3 * n * 8 + 2 * lbm.NTOTALS * 8
+    e2e_mlups = 2 * n * K * ws / e2e_s / 1e6
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "D3Q19 CG + SC multiphase oscillating droplet, 128^3 each, FP32",
+                       "lattice": "D3Q19", "nx": N3, "ny": N3, "nz": N3, "density_ratio": 10,
+                       "cg": {"A": 5e-3, "tau": 1.0, "beta": 0.7}, "sc": {"G": -5.0, "rho0": 1.0, "tau": 1.0},
+                       "l2": "inputs larger than L2 (477 MB of populations per step)",
+                       "parallelism": f"replicas x{ws}"},
+            "cg_mlups": n / (cg_avg / 1e3) / 1e6, "sc_mlups": n / (sc_avg / 1e3) / 1e6,
+            "cg_step_ms": cg_avg, "sc_step_ms": sc_avg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "step_kernel<D3Q19,float,CG>",
+                         "bytes_per_lu": BYTES_PER_LU["cg"], "peak_kind": peak_kind,
+                         "sc": {"achieved": BYTES_PER_LU["sc"] * n / (sc_avg / 1e3) / 1e9,
+                                "frac": BYTES_PER_LU["sc"] * n / (sc_avg / 1e3) / 1e9 / peak}},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                    "request": f"init from pinned host fields + {K} CG and {K} SC steps + densities/totals to host"},
+            "gpu_launches": launches,
+            "status": {"cg": lbm.status_string(rc_cg), "sc": lbm.status_string(rc_sc),
+                       "cg_mass_r": tot_cg["mass_r"], "sc_mass": tot_sc["mass_r"]},
+        }
+        if not args.no_cpu_baseline:
+            mlups_cpu, cores, dt, ns = oracle_sample_mlups(2, 16)
+            line["cpu_baseline"] = {"value": mlups_cpu, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                    "sample": f"FP64 oracle, 2 CG + 2 SC steps on a 128x128x16 slab of the "
+                                              f"workload ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", default=None, choices=["cg", "sc"],
+                    help="profiling runs: warm up and step only this lattice, print nothing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * lbm.h -- C ABI of the GB300 two-component lattice Boltzmann library (liblbm.so).
+ *
+ * The library advances one lattice of either model compared in arXiv 2110.05197
+ * (Datadien, Di Staso, Wijshoff & Toschi):
+ *   - the colour-gradient (CG) model of Sec. 2.2: two population sets (red, blue), BGK
+ *     towards the enhanced equilibrium (Eq. equiliCG), the surface-tension perturbation
+ *     (Eq. perturbationOp), recolouring (Eqs. recoloringOpR/B), optionally the
+ *     inter-interface repulsion force of Sec. 2.3 (Eq. repForce), then streaming
+ *     (Eq. streaming);
+ *   - the Shan-Chen (SC) model of Sec. 2.1: the multiphase pseudopotential force
+ *     (Eqs. interactionforceMP, pseudopotential) or the two-component cross force
+ *     (Eq. doublebeltrepulsionforce2), Guo forcing (Eqs. guoforce, source, guoforce2),
+ *     BGK (Eqs. collisSC, equiliSC), streaming (Eq. streamingSC).
+ * The problem statement the calls follow is the paper's: initialise the component
+ * densities (and velocity) on a periodic box (Sec. 3), evolve a number of steps, measure
+ * moments (Sec. 3.1, Eqs. YoungLaplace..rhoout; Sec. 3.2).
+ *
+ * Conventions
+ *   - Every call returns an lbm_status; nothing is thrown across the ABI.  After a CUDA
+ *     error the context keeps the first error (sticky) and every later call returns it.
+ *   - The caller owns all device memory and the stream.  lbm_create only reports the
+ *     workspace size it needs (ws == NULL) or binds the caller's workspace; the library
+ *     never allocates device memory.  The context object itself is a small host struct.
+ *   - All device work is enqueued on the stream given to lbm_create.  Calls return without
+ *     synchronising, except where a host pointer is read or written (see below).
+ *   - Lattice layout: node = x + nx*(y + ny*z), x fastest.  Populations are
+ *     structure-of-arrays [component][direction][node].  Direction order (the paper lists
+ *     only the groups, Eq. speeds):
+ *       D3Q19: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),(-1,-1,0),(1,-1,0),
+ *              (-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),
+ *              (0,-1,1);
+ *       D2Q9:  0 rest; 1..4 = +x,-x,+y,-y; 5..8 = (1,1),(-1,-1),(1,-1),(-1,1).
+ *     The opposite of odd direction i >= 1 is i+1.
+ *   - Pointer arguments of lbm_init_fields and lbm_moments may be device pointers or host
+ *     pointers (pinned or pageable); the library inspects each one.  Host data is staged
+ *     through the workspace with cudaMemcpyAsync on the context's stream; a call that reads
+ *     or writes a host pointer synchronises that stream before returning.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,     /* bad argument: NULL where required, size or parameter out of range */
+  LBM_ENOMEM = 2,     /* workspace smaller than lbm_create reported */
+  LBM_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed (sticky) */
+  LBM_EUNSTABLE = 4,  /* the blow-up check tripped: non-finite, negative density or |u| too large */
+  LBM_ESTATE = 5,     /* call does not fit the context: wrong model for this step call, or
+                         stepping before lbm_init_fields */
+  LBM_ETIMEOUT = 6    /* a bounded device wait gave up (reserved for the batched engine) */
+} lbm_status;
+
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+enum { LBM_MODEL_CG = 0, LBM_MODEL_SC_MP = 1, LBM_MODEL_SC_2C = 2 };
+/* Storage precision of the populations.  FP64 computes in FP64; the others compute in FP32.
+ * Populations are stored as deviations from the rest-state equilibrium of each node's
+ * density one step earlier (kept in a reference field, FP64 for LBM_FP64, FP32 otherwise),
+ * so 16-bit storage holds only the small non-equilibrium and velocity parts. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
+enum { LBM_NTOTALS = 10 };
+
+/* Parameters of one lattice.  Field meanings follow the paper's notation. */
+typedef struct {
+  int32_t lattice;        /* LBM_D2Q9 (nz must be 1) or LBM_D3Q19 */
+  int32_t model;          /* LBM_MODEL_CG, LBM_MODEL_SC_MP (one set), LBM_MODEL_SC_2C (two sets) */
+  int32_t precision;      /* LBM_FP64, LBM_FP32, LBM_FP16 or LBM_BF16 (see above) */
+  int32_t nx, ny, nz;     /* lattice size, each >= 1; periodic in every direction */
+  double rho_r0, rho_b0;  /* CG bulk densities; density ratio gamma = rho_r0/rho_b0 (Eq. gamma) */
+  double alpha_b;         /* CG rest parameter of the blue fluid (0.2 in the paper); alpha_R from
+                             Eq. gamma */
+  double tau_r, tau_b;    /* relaxation times (> 1/2); nu_k = (tau_k - 1/2)/3; SC multiphase
+                             uses tau_r */
+  double A, beta;         /* CG perturbation amplitude (sigma = 4/9 A/omega_eff, Eq. sigmaA) and
+                             recolouring parameter (0.7 in the paper) */
+  int32_t enhanced_eq;    /* 1: enhanced equilibrium of Eq. equiliCG; 0: its plain second-order
+                             part (the "standard" CG of Sec. 3.3) */
+  int32_t color_norm;     /* 0: rho^N = (rho_R - rho_B)/(rho_R + rho_B) as printed; 1: each
+                             density divided by its bulk value rho_k0 first */
+  double rep_pi, rep_chi; /* CG repulsion: Pi (0 disables the force) and chi (Eq. potential) */
+  int32_t rep_psi_kind;   /* 0: psi_rep = (1 - |rho^N|)^chi; 1: (1 + |rho^N|)^chi as printed */
+  double grad_eps;        /* |grad rho^N| <= grad_eps: no perturbation, cos(phi_i) = 0, no normal */
+  double G, rho0_psi;     /* SC coupling G and reference density rho_0 (multiphase psi) or
+                             rho_0^(s) (two-component cross force) */
+  double body_force[3];   /* constant body-force density (Guo forcing); 0 for none */
+  int32_t diag_every;     /* run the blow-up check every n steps inside lbm_step_*; 0 = never */
+  double umax_unstable;   /* blow-up threshold on |u| (default used when <= 0: 0.5) */
+} lbm_params;
+
+/* Validate p and size the workspace.
+ *   ws == NULL: write the required workspace size (bytes) to *ws_bytes and return LBM_OK;
+ *               *out is left untouched.
+ *   ws != NULL: ws must be a device buffer of at least the required size, 256-byte aligned,
+ *               owned by the caller and kept alive until lbm_destroy; *ws_bytes gives its
+ *               size (LBM_ENOMEM if too small).  Creates the context in *out.
+ * stream is a cudaStream_t (NULL = legacy default stream) on which all work is enqueued.
+ * Errors: LBM_EINVAL for NULL p/ws_bytes/out or parameters out of range. */
+lbm_status lbm_create(const lbm_params* p, void* ws, size_t* ws_bytes, void* stream, lbm_ctx** out);
+
+/* Set the initial state (Sec. 3: sharp-interface component densities, optional velocity).
+ *   rho_r [N]: density of component R (CG red / SC multiphase rho / SC species 1); required.
+ *   rho_b [N]: density of component B (CG blue / SC species 2); ignored for SC multiphase.
+ *   u [3][N] (component-major), solid [N] (uint8, 1 = wall node), pops [K][Q][N]: optional.
+ * All floating-point inputs are FP64.  With pops != NULL the populations are taken from it
+ * (checkpoint restore, canonical order, rho_r/rho_b/u unused but rho_r must be non-NULL);
+ * otherwise f^k = f^{k,eq}(rho_k, u, grad rho_k) (CG, Eq. equiliCG) or f^eq(rho_s, u)
+ * (SC, Eq. equiliSC).  Wall nodes hold no populations.  Resets the step counter and the
+ * blow-up status.  Reads host pointers synchronously. */
+lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho_r, const double* rho_b, const double* u,
+                           const uint8_t* solid, const double* pops);
+
+/* Advance nsteps (>= 0) colour-gradient steps.  LBM_ESTATE if the model is not CG or the
+ * fields were never initialised.  Asynchronous. */
+lbm_status lbm_step_cg(lbm_ctx* ctx, int32_t nsteps);
+
+/* Advance nsteps (>= 0) Shan-Chen steps (multiphase or two-component, by model).
+ * LBM_ESTATE if the model is CG or the fields were never initialised.  Asynchronous. */
+lbm_status lbm_step_sc(lbm_ctx* ctx, int32_t nsteps);
+
+/* Moments of the current state.  Every output may be NULL.  Outputs are FP64:
+ *   rho_r, rho_b [N]; u [3][N] = (sum_k sum_i f c_i + F/2)/rho, the force-shifted velocity of
+ *   Eq. guoforce (0 on wall nodes); pops [K][Q][N] canonical post-streaming populations;
+ *   totals (HOST, LBM_NTOTALS doubles): mass_r, mass_b, momentum x/y/z (sum_k sum_i f c_i),
+ *   E_kin = sum 1/2 rho |u|^2, max |u|, count of nodes with a non-finite population,
+ *   min rho_r, min rho_b -- over fluid nodes, reduced in FP64 in a fixed order.
+ * totals != NULL synchronises the stream and returns LBM_EUNSTABLE when the blow-up check
+ * trips (a non-finite population, a density below -1e-6 times the larger bulk density, or
+ * max|u| > umax_unstable), also when a
+ * periodic in-step check (diag_every) tripped earlier. */
+lbm_status lbm_moments(lbm_ctx* ctx, double* rho_r, double* rho_b, double* u, double* pops,
+                       double* totals);
+
+/* Release the host-side context.  NULL-safe.  Does not free the caller's workspace. */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* lbm_status_string(lbm_status s);
+
+/* Tiling of the fused step kernel: a block owns tx * ty columns (tx * ty <= 256 and a
+ * multiple of 32) and marches tz z-planes (tz must be 1 for D2Q9).  Default 32 x 8 x 16.
+ * Changes only the launch shape; results are bitwise independent of it.  LBM_EINVAL
+ * for shapes outside those limits. */
+lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t tx, int32_t ty, int32_t tz);
+
+/* Number of kernel launches this context has enqueued since creation (for accounting). */
+uint64_t lbm_launch_count(const lbm_ctx* ctx);
+
+/* Exact checkpoint of the raw device state (stored deviations and reference densities),
+ * for bitwise resume on the same precision and lattice; lbm_moments' canonical populations
+ * are the portable FP64 form.  lbm_state_bytes: size of that state (0 for NULL).
+ * lbm_save_state copies it to dst (host or device, caller-owned, lbm_state_bytes large),
+ * synchronously; returns LBM_EUNSTABLE (state still written) if the blow-up check had
+ * tripped.  lbm_load_state restores it (solid: the wall mask as for lbm_init_fields, or
+ * NULL), synchronously, and resets the step counter and blow-up status. */
+size_t lbm_state_bytes(const lbm_ctx* ctx);
+lbm_status lbm_save_state(lbm_ctx* ctx, void* dst);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, const uint8_t* solid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,388 @@
+// C ABI of liblbm.so (declared in include/lbm.h): context creation over a caller-owned
+// workspace, initial state, stepping and moments.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "lbm_internal.cuh"
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+bool params_ok(const lbm_params* p) {
+  if (!p) return false;
+  if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return false;
+  if (p->model < LBM_MODEL_CG || p->model > LBM_MODEL_SC_2C) return false;
+  if (p->precision < LBM_FP64 || p->precision > LBM_BF16) return false;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
+  if (p->lattice == LBM_D2Q9 && p->nz != 1) return false;
+  const long long n = (long long)p->nx * p->ny * p->nz;
+  if (n > (1LL << 31)) return false;
+  if (!(p->tau_r > 0.5)) return false;
+  if (p->model != LBM_MODEL_SC_MP && !(p->tau_b > 0.5)) return false;
+  if (p->model == LBM_MODEL_CG) {
+    if (!(p->rho_r0 > 0) || !(p->rho_b0 > 0) || !(p->alpha_b >= 0 && p->alpha_b < 1)) return false;
+    const double ar = 1.0 - (1.0 - p->alpha_b) * p->rho_b0 / p->rho_r0;
+    if (!(ar >= 0 && ar < 1)) return false;
+    if (!(p->grad_eps >= 0)) return false;
+  } else {
+    if (!(p->rho0_psi > 0)) return false;
+  }
+  if (p->diag_every < 0) return false;
+  return true;
+}
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+lbm_status fail(lbm_ctx* c, cudaError_t e) {
+  if (e == cudaSuccess) return LBM_OK;
+  if (c->sticky == LBM_OK) c->sticky = LBM_ECUDA;
+  return LBM_ECUDA;
+}
+
+// Device view of a caller buffer of `bytes`: the pointer itself when it is device
+// memory, otherwise `stage` after an H2D copy.
+cudaError_t stage_in(lbm_ctx* c, const void* src, size_t bytes, void* stage, const void** dev, bool* host) {
+  if (is_device_ptr(src)) {
+    *dev = src;
+    return cudaSuccess;
+  }
+  *host = true;
+  *dev = stage;
+  return cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, c->stream);
+}
+
+cudaError_t copy_out(lbm_ctx* c, void* dst, const void* src, size_t bytes, bool* host) {
+  if (!is_device_ptr(dst)) *host = true;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
+}
+
+}  // namespace
+
+namespace lbm {
+
+size_t workspace_layout(const lbm_params& p, lbm_ctx* c) {
+  const int K = p.model == LBM_MODEL_SC_MP ? 1 : 2;
+  const int Q = p.lattice == LBM_D3Q19 ? 19 : 9;
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  const size_t elt = p.precision == LBM_FP64 ? 8 : (p.precision == LBM_FP32 ? 4 : 2);
+  const size_t relt = p.precision == LBM_FP64 ? 8 : 4;
+  const int nblk = (int)std::min<long long>((N + kDiagThreads - 1) / kDiagThreads, 1184);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += align256(b);
+    return o;
+  };
+  const size_t of0 = take((size_t)K * Q * N * elt);
+  const size_t of1 = take((size_t)K * Q * N * elt);
+  const size_t or0 = take((size_t)K * N * relt);
+  const size_t or1 = take((size_t)K * N * relt);
+  const size_t osol = take((size_t)N);
+  const size_t ostg = take((size_t)5 * N * sizeof(double));
+  const size_t opar = take((size_t)nblk * LBM_NTOTALS * sizeof(double));
+  const size_t odia = take(sizeof(lbm_diag));
+  if (c) {
+    c->K = K;
+    c->Q = Q;
+    c->N = N;
+    c->elt = elt;
+    c->relt = relt;
+    c->f[0] = c->ws + of0;
+    c->f[1] = c->ws + of1;
+    c->r[0] = c->ws + or0;
+    c->r[1] = c->ws + or1;
+    c->solid = reinterpret_cast<uint8_t*>(c->ws + osol);
+    c->stage = reinterpret_cast<double*>(c->ws + ostg);
+    c->partials = reinterpret_cast<double*>(c->ws + opar);
+    c->nblk_diag = nblk;
+    c->diag = reinterpret_cast<lbm_diag*>(c->ws + odia);
+  }
+  return off;
+}
+
+size_t step_smem_for(const lbm_ctx* c, int tx, int ty) {
+  const size_t ne = size_t(tx + 2) * (ty + 2), ni = size_t(tx) * ty;
+  const int npl = c->p.lattice == LBM_D3Q19 ? 3 : 1;
+  const int nf = c->p.model == LBM_MODEL_SC_MP ? 1 : 2;
+  const size_t t = c->p.precision == LBM_FP64 ? 8 : 4;  // compute type
+  return npl * (nf + c->K) * ne * t + 2 * c->K * (c->Q + 1) * ni * t + (c->has_walls ? npl * ne : 0);
+}
+
+static cudaError_t launch_step(lbm_ctx* c) {
+  switch (c->p.precision) {
+    case LBM_FP64: return launch_step_f64(c);
+    case LBM_FP32: return launch_step_f32(c);
+    case LBM_FP16: return launch_step_f16(c);
+    default: return launch_step_bf16(c);
+  }
+}
+
+}  // namespace lbm
+
+extern "C" {
+
+const char* lbm_status_string(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "workspace too small";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EUNSTABLE: return "simulation unstable (blow-up check tripped)";
+    case LBM_ESTATE: return "call does not fit the context state or model";
+    case LBM_ETIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+lbm_status lbm_create(const lbm_params* p, void* ws, size_t* ws_bytes, void* stream, lbm_ctx** out) {
+  if (!p || !ws_bytes || !params_ok(p)) return LBM_EINVAL;
+  const size_t need = lbm::workspace_layout(*p, nullptr);
+  if (!ws) {
+    *ws_bytes = need;
+    return LBM_OK;
+  }
+  if (!out) return LBM_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LBM_EINVAL;
+  if (*ws_bytes < need) return LBM_ENOMEM;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ENOMEM;
+  c->p = *p;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->ws = static_cast<unsigned char*>(ws);
+  c->ws_bytes = *ws_bytes;
+  lbm::workspace_layout(*p, c);
+  c->cur = 0;
+  c->has_walls = false;
+  c->initialised = false;
+  c->sticky = LBM_OK;
+  c->launches = 0;
+  c->steps = 0;
+  c->tx = 32;
+  c->ty = 8;
+  c->tz = p->lattice == LBM_D3Q19 ? (p->nz < 16 ? p->nz : 16) : 1;
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_tiling(lbm_ctx* c, int32_t tx, int32_t ty, int32_t tz) {
+  if (!c) return LBM_EINVAL;
+  if (tx < 1 || ty < 1 || tz < 1 || tx * ty > 256 || (tx * ty) % 32 != 0) return LBM_EINVAL;
+  if (c->p.lattice == LBM_D2Q9 && tz != 1) return LBM_EINVAL;
+  c->tx = tx;
+  c->ty = ty;
+  c->tz = tz;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx* c, const double* rho_r, const double* rho_b, const double* u,
+                           const uint8_t* solid, const double* pops) {
+  if (!c) return LBM_EINVAL;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!rho_r) return LBM_EINVAL;
+  if (c->K == 2 && !rho_b && !pops) return LBM_EINVAL;
+  const long long N = c->N;
+  bool host = false;
+  cudaError_t e;
+  // wall mask
+  if (solid) {
+    if (is_device_ptr(solid))
+      e = cudaMemcpyAsync(c->solid, solid, N, cudaMemcpyDeviceToDevice, c->stream);
+    else {
+      host = true;
+      e = cudaMemcpyAsync(c->solid, solid, N, cudaMemcpyHostToDevice, c->stream);
+    }
+    c->has_walls = true;
+  } else {
+    e = cudaMemsetAsync(c->solid, 0, N, c->stream);
+    c->has_walls = false;
+  }
+  if (e != cudaSuccess) return fail(c, e);
+  if (pops) {
+    // pass 1: component densities into stage[0, K*N); pass 2: deviations relative to them
+    const bool dev = is_device_ptr(pops);
+    double* acc = c->stage;
+    double* buf = c->stage + 2 * N;
+    for (int pass = 0; pass < 2; pass++)
+      for (int k = 0; k < c->K; k++)
+        for (int i = 0; i < c->Q; i++) {
+          const double* src = pops + (size_t)(k * c->Q + i) * N;
+          const double* plane = src;
+          if (!dev) {
+            host = true;
+            e = cudaMemcpyAsync(buf, src, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) return fail(c, e);
+            plane = buf;
+          }
+          e = pass == 0 ? lbm::launch_restore_accumulate(c, plane, k, acc, i == 0)
+                        : lbm::launch_restore_plane(c, plane, k, i, acc);
+          if (e != cudaSuccess) return fail(c, e);
+        }
+  } else {
+    const void *drr = nullptr, *drb = nullptr, *du = nullptr;
+    e = stage_in(c, rho_r, N * sizeof(double), c->stage, &drr, &host);
+    if (e == cudaSuccess && c->K == 2) e = stage_in(c, rho_b, N * sizeof(double), c->stage + N, &drb, &host);
+    if (e == cudaSuccess && u) e = stage_in(c, u, 3 * N * sizeof(double), c->stage + 2 * N, &du, &host);
+    if (e != cudaSuccess) return fail(c, e);
+    if (c->K == 1) drb = drr;  // unused by the multiphase equilibrium
+    e = lbm::launch_init_eq(c, static_cast<const double*>(drr), static_cast<const double*>(drb),
+                            static_cast<const double*>(du));
+    if (e != cudaSuccess) return fail(c, e);
+  }
+  e = cudaMemsetAsync(c->diag, 0, sizeof(lbm_diag), c->stream);
+  if (e != cudaSuccess) return fail(c, e);
+  if (host) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, e);
+  }
+  c->cur = 0;
+  c->steps = 0;
+  c->initialised = true;
+  return LBM_OK;
+}
+
+static lbm_status step_common(lbm_ctx* c, int32_t nsteps, bool cg) {
+  if (!c || nsteps < 0) return LBM_EINVAL;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!c->initialised) return LBM_ESTATE;
+  if (cg != (c->p.model == LBM_MODEL_CG)) return LBM_ESTATE;
+  for (int s = 0; s < nsteps; s++) {
+    cudaError_t e = lbm::launch_step(c);
+    if (e != cudaSuccess) return fail(c, e);
+    c->launches += 1;
+    c->cur ^= 1;
+    c->steps += 1;
+    if (c->p.diag_every > 0 && c->steps % c->p.diag_every == 0) {
+      e = lbm::launch_diagnostics(c, nullptr, false);
+      if (e != cudaSuccess) return fail(c, e);
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_step_cg(lbm_ctx* c, int32_t nsteps) { return step_common(c, nsteps, true); }
+lbm_status lbm_step_sc(lbm_ctx* c, int32_t nsteps) { return step_common(c, nsteps, false); }
+
+lbm_status lbm_moments(lbm_ctx* c, double* rho_r, double* rho_b, double* u, double* pops, double* totals) {
+  if (!c) return LBM_EINVAL;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!c->initialised) return LBM_ESTATE;
+  const long long N = c->N;
+  bool host = false;
+  cudaError_t e = cudaSuccess;
+  const bool need_diag = rho_r || rho_b || u || totals;
+  if (need_diag) {
+    double* u_dev = (u && is_device_ptr(u)) ? u : nullptr;
+    e = lbm::launch_diagnostics(c, u_dev, u != nullptr);
+    if (e != cudaSuccess) return fail(c, e);
+    if (rho_r) e = copy_out(c, rho_r, c->stage, N * sizeof(double), &host);
+    if (e == cudaSuccess && rho_b) e = copy_out(c, rho_b, c->stage + N, N * sizeof(double), &host);
+    if (e == cudaSuccess && u && !u_dev) e = copy_out(c, u, c->stage + 2 * N, 3 * N * sizeof(double), &host);
+    if (e != cudaSuccess) return fail(c, e);
+  }
+  if (pops) {
+    if (is_device_ptr(pops)) {
+      e = lbm::launch_export_all(c, pops);
+      if (e != cudaSuccess) return fail(c, e);
+    } else {
+      host = true;
+      // the staged densities/velocity were already copied out (stream order)
+      for (int k = 0; k < c->K; k++)
+        for (int i = 0; i < c->Q; i++) {
+          e = lbm::launch_export_plane(c, c->stage, k, i);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pops + (size_t)(k * c->Q + i) * N, c->stage, N * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream);
+          if (e != cudaSuccess) return fail(c, e);
+        }
+    }
+  }
+  lbm_diag hd;
+  if (totals) {
+    e = cudaMemcpyAsync(&hd, c->diag, sizeof(lbm_diag), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return fail(c, e);
+    host = true;
+  }
+  if (host) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, e);
+  }
+  if (totals) {
+    std::memcpy(totals, hd.totals, sizeof(hd.totals));
+    if (hd.status != 0) return LBM_EUNSTABLE;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+  delete c;
+  return LBM_OK;
+}
+
+uint64_t lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
+
+size_t lbm_state_bytes(const lbm_ctx* c) {
+  if (!c) return 0;
+  return (size_t)c->K * c->Q * c->N * c->elt + (size_t)c->K * c->N * c->relt;
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* dst) {
+  if (!c || !dst) return LBM_EINVAL;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!c->initialised) return LBM_ESTATE;
+  // the blow-up status decides which buffer pair is the state; read it first
+  lbm_diag hd;
+  cudaError_t e = cudaMemcpyAsync(&hd, c->diag, sizeof(lbm_diag), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, e);
+  const int b = hd.status ? hd.trip_buf : c->cur;
+  const size_t fb = (size_t)c->K * c->Q * c->N * c->elt;
+  e = cudaMemcpyAsync(dst, c->f[b], fb, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(static_cast<char*>(dst) + fb, c->r[b], (size_t)c->K * c->N * c->relt, cudaMemcpyDefault,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, e);
+  return hd.status ? LBM_EUNSTABLE : LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* src, const uint8_t* solid) {
+  if (!c || !src) return LBM_EINVAL;
+  if (c->sticky != LBM_OK) return c->sticky;
+  const long long N = c->N;
+  cudaError_t e;
+  if (solid) {
+    e = cudaMemcpyAsync(c->solid, solid, N, cudaMemcpyDefault, c->stream);
+    c->has_walls = true;
+  } else {
+    e = cudaMemsetAsync(c->solid, 0, N, c->stream);
+    c->has_walls = false;
+  }
+  const size_t fb = (size_t)c->K * c->Q * N * c->elt;
+  const size_t rb = (size_t)c->K * N * c->relt;
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+    e = cudaMemcpyAsync(c->f[b], src, fb, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->r[b], static_cast<const char*>(src) + fb, rb, cudaMemcpyDefault, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->diag, 0, sizeof(lbm_diag), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail(c, e);
+  c->cur = 0;
+  c->steps = 0;
+  c->initialised = true;
+  return LBM_OK;
+}
+
+}  // extern "C"

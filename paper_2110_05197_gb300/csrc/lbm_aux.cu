@@ -1,0 +1,492 @@
+// Auxiliary kernels: equilibrium initialisation, checkpoint import/export of populations,
+// and the FP64 moment / diagnostics reductions (mass, momentum, E_kin, max|u|, blow-up).
+//
+// Populations are stored as deviations g^k_i = f^k_i - phi^k_i r_k from the rest-state
+// equilibrium of a per-node reference density r_k (see lbm_step.cuh); every kernel here
+// reconstructs f in FP64 as g + phi r.
+#include <cmath>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+namespace {
+
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(__half v) { return (double)__half2float(v); }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <class S>
+__device__ __forceinline__ S from_d(double v);
+template <>
+__device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ __half from_d<__half>(double v) { return __float2half_rn((float)v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+
+__device__ __forceinline__ long long nb_index(int x, int y, int z, int dx, int dy, int dz, int nx, int ny, int nz) {
+  x += dx;
+  y += dy;
+  z += dz;
+  x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+  z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+  return x + (long long)nx * (y + (long long)ny * z);
+}
+
+struct AuxParams {
+  int nx, ny, nz;
+  long long n;
+  int model, enhanced, K;
+  double phi[2][3];      // rest-state weights per component and group
+  double nu_r, nu_b;
+  double G, rho0;        // SC two-component: G = G_eff
+  double body[3];
+  double umax, neg_tol;
+};
+
+AuxParams aux_params(const lbm_ctx* c) {
+  const lbm_params& q = c->p;
+  AuxParams a{};
+  a.nx = q.nx;
+  a.ny = q.ny;
+  a.nz = q.nz;
+  a.n = c->N;
+  a.model = q.model;
+  a.enhanced = q.enhanced_eq;
+  a.K = c->K;
+  rest_weights(q, a.phi);
+  a.nu_r = (q.tau_r - 0.5) / 3.0;
+  a.nu_b = (q.tau_b - 0.5) / 3.0;
+  a.G = q.model == LBM_MODEL_SC_2C ? q.G / (q.rho0_psi * q.rho0_psi) : q.G;
+  a.rho0 = q.rho0_psi;
+  for (int d = 0; d < 3; d++) a.body[d] = q.body_force[d];
+  a.umax = q.umax_unstable > 0 ? q.umax_unstable : 0.5;
+  double scale = 1.0;
+  if (q.model == LBM_MODEL_CG) scale = fmax(scale, fmax(q.rho_r0, q.rho_b0));
+  a.neg_tol = 1e-6 * scale;
+  return a;
+}
+
+// The buffer pair holding the current state: the host's index, or the pair frozen by a
+// tripped blow-up check (the host cannot know when that happened).
+__device__ __forceinline__ int state_index(const lbm_diag* d, int cur) { return d->status ? d->trip_buf : cur; }
+
+// 3 sum_i w_i phi(x + c_i) c_i with a wall neighbour replaced by the centre value.
+template <class L>
+__device__ void grad_fp64(const double* phi, const uint8_t* solid, long long n, int x, int y, int z,
+                          const AuxParams& a, double g[3]) {
+  g[0] = g[1] = g[2] = 0.0;
+  for (int q = 0; q < L::NP; q++) {
+    const int i = 2 * q + 1;
+    const long long mp = nb_index(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
+    const long long mm = nb_index(x, y, z, -cx<L>(i), -cy<L>(i), -cz<L>(i), a.nx, a.ny, a.nz);
+    const double vp = (solid && solid[mp]) ? phi[n] : phi[mp];
+    const double vm = (solid && solid[mm]) ? phi[n] : phi[mm];
+    const double d = 3.0 * L::w(L::pgrp(q)) * (vp - vm);
+    g[0] += L::pcx(q) * d;
+    g[1] += L::pcy(q) * d;
+    g[2] += L::pcz(q) * d;
+  }
+}
+
+// Eq. equiliCG for one colour (phi from Eq. phi, enhanced part optional) or Eq. equiliSC
+// (phi = w, no enhanced part), minus phi_i * rref, into out[Q].
+template <class L>
+__device__ void feq_dev(double rho_k, const double* phi, double nubar_en, const double u[3], const double g[3],
+                        double rref, double* out) {
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+  for (int i = 0; i < L::Q; i++) {
+    const int gr = grp<L>(i);
+    const double cu = cx<L>(i) * u[0] + cy<L>(i) * u[1] + cz<L>(i) * u[2];
+    const double cgr = cx<L>(i) * g[0] + cy<L>(i) * g[1] + cz<L>(i) * g[2];
+    const double w = L::w(gr);
+    const double enh = nubar_en * (L::psi(gr) * ug + 2.0 * L::xi(gr) * cu * cgr);
+    out[i] = enh + phi[gr] * (rho_k - rref) + rho_k * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+  }
+}
+
+template <class L, class S, class RT>
+__global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __restrict__ ra, RT* __restrict__ rb_,
+                               const double* __restrict__ rr, const double* __restrict__ rb,
+                               const double* __restrict__ U, const uint8_t* __restrict__ solid, AuxParams a) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
+    double out[L::Q];
+    if (solid && solid[n]) {
+      for (int k = 0; k < a.K; k++) {
+        ra[(long long)k * a.n + n] = RT(0);
+        rb_[(long long)k * a.n + n] = RT(0);
+        for (int i = 0; i < L::Q; i++) {
+          fa[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(0.0);
+          fb[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(0.0);
+        }
+      }
+      continue;
+    }
+    const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+    double u[3] = {0.0, 0.0, 0.0};
+    if (U) {
+      u[0] = U[n];
+      u[1] = U[a.n + n];
+      u[2] = U[2 * a.n + n];
+    }
+    for (int k = 0; k < a.K; k++) {
+      const double* phi = k == 0 ? rr : rb;
+      const RT rref = RT(phi[n]);  // reference density: the initial density, rounded
+      double g[3] = {0.0, 0.0, 0.0};
+      double en = 0.0;
+      if (a.model == LBM_MODEL_CG) {
+        grad_fp64<L>(phi, solid, n, x, y, z, a, g);
+        const double r = rr[n], b = rb[n], rho = r + b;
+        const double nubar = 1.0 / ((r / rho) / a.nu_r + (b / rho) / a.nu_b);  // Eq. interpVisc
+        en = a.enhanced ? nubar : 0.0;
+      }
+      feq_dev<L>(phi[n], a.phi[k], en, u, g, (double)rref, out);
+      ra[(long long)k * a.n + n] = rref;
+      rb_[(long long)k * a.n + n] = rref;
+      for (int i = 0; i < L::Q; i++) {
+        fa[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(out[i]);
+        fb[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(out[i]);
+      }
+    }
+  }
+}
+
+__global__ void restore_acc_kernel(const double* __restrict__ plane, double* __restrict__ acc, long long n, bool first) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x)
+    acc[m] = first ? plane[m] : acc[m] + plane[m];
+}
+
+template <class S, class RT>
+__global__ void restore_plane_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __restrict__ ra,
+                                     RT* __restrict__ rb_, const double* __restrict__ plane,
+                                     const double* __restrict__ acc, const uint8_t* __restrict__ solid, long long n,
+                                     long long off, long long roff, double phi, bool write_ref) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+    const bool wall = solid && solid[m];
+    const RT r = wall ? RT(0) : RT(acc[m]);
+    const S v = wall ? from_d<S>(0.0) : from_d<S>(plane[m] - phi * (double)r);
+    fa[off + m] = v;
+    fb[off + m] = v;
+    if (write_ref) {
+      ra[roff + m] = r;
+      rb_[roff + m] = r;
+    }
+  }
+}
+
+// canonical populations f = g + phi r, FP64; `out` holds planes [first_plane, first_plane+np)
+template <class L, class S, class RT>
+__global__ void export_kernel(const S* __restrict__ f0, const S* __restrict__ f1, const RT* __restrict__ r0,
+                              const RT* __restrict__ r1, const lbm_diag* __restrict__ d, int cur, int first_plane,
+                              int np, double* __restrict__ out, AuxParams a) {
+  const int b = state_index(d, cur);
+  const S* f = b ? f1 : f0;
+  const RT* r = b ? r1 : r0;
+  const long long total = (long long)np * a.n;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < total; m += (long long)gridDim.x * blockDim.x) {
+    const int plane = first_plane + (int)(m / a.n);
+    const long long node = m - (long long)(plane - first_plane) * a.n;
+    const int k = plane / L::Q, i = plane - k * L::Q;
+    out[m] = to_d(f[(long long)plane * a.n + node]) + a.phi[k][grp<L>(i)] * to_d(r[(long long)k * a.n + node]);
+  }
+}
+
+template <class L, class S, class RT>
+__global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__ f1, const RT* __restrict__ r0,
+                                 const RT* __restrict__ r1, const lbm_diag* __restrict__ d, int cur,
+                                 double* __restrict__ rr, double* __restrict__ rb, AuxParams a) {
+  const int b = state_index(d, cur);
+  const S* f = b ? f1 : f0;
+  const RT* r = b ? r1 : r0;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+    for (int k = 0; k < 2; k++) {
+      double s = 0.0;
+      if (k < a.K) {
+        for (int i = 0; i < L::Q; i++) s += to_d(f[(long long)(k * L::Q + i) * a.n + m]);
+        s += to_d(r[(long long)k * a.n + m]);  // sum_i phi_i = 1
+      }
+      (k == 0 ? rr : rb)[m] = s;
+    }
+  }
+}
+
+// ---- fixed-order block reductions ----
+struct Acc {
+  double v[LBM_NTOTALS];
+};
+// slots: 0 mass_r 1 mass_b 2-4 mom 5 ekin 6 max|u| 7 nonfinite 8 min rr 9 min rb
+__device__ __forceinline__ void acc_init(Acc& a) {
+  for (int s = 0; s < LBM_NTOTALS; s++) a.v[s] = 0.0;
+  a.v[8] = INFINITY;
+  a.v[9] = INFINITY;
+}
+__device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
+  for (int s = 0; s < 6; s++) a.v[s] += b.v[s];
+  a.v[6] = fmax(a.v[6], b.v[6]);
+  a.v[7] += b.v[7];
+  a.v[8] = fmin(a.v[8], b.v[8]);
+  a.v[9] = fmin(a.v[9], b.v[9]);
+}
+__device__ void block_reduce(Acc& a) {
+  __shared__ double sh[kDiagThreads / 32][LBM_NTOTALS];
+  for (int off = 16; off > 0; off >>= 1) {
+    Acc o;
+    for (int s = 0; s < LBM_NTOTALS; s++) o.v[s] = __shfl_xor_sync(0xffffffffu, a.v[s], off);
+    acc_merge(a, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int s = 0; s < LBM_NTOTALS; s++) sh[warp][s] = a.v[s];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+      Acc o;
+      for (int s = 0; s < LBM_NTOTALS; s++) o.v[s] = sh[w][s];
+      acc_merge(a, o);
+    }
+  }
+}
+
+template <class L, class S, class RT>
+__global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict__ f0, const S* __restrict__ f1,
+                                                            const RT* __restrict__ r0, const RT* __restrict__ r1,
+                                                            const lbm_diag* __restrict__ d, int cur,
+                                                            const double* __restrict__ rr,
+                                                            const double* __restrict__ rb,
+                                                            const uint8_t* __restrict__ solid, double* __restrict__ uo,
+                                                            double* __restrict__ partials, AuxParams a) {
+  const int bsel = state_index(d, cur);
+  const S* f = bsel ? f1 : f0;
+  const RT* rref = bsel ? r1 : r0;
+  Acc acc;
+  acc_init(acc);
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
+    const bool wall = solid && solid[n];
+    double j[3] = {0.0, 0.0, 0.0};
+    int bad = 0;
+    for (int k = 0; k < a.K; k++) {
+      const double rk = to_d(rref[(long long)k * a.n + n]);
+      if (!isfinite(rk)) bad = 1;
+      for (int i = 0; i < L::Q; i++) {
+        // the shift phi_i r is symmetric in c_i and carries no momentum
+        const double v = to_d(f[(long long)(k * L::Q + i) * a.n + n]);
+        if (!isfinite(v)) bad = 1;
+        j[0] += cx<L>(i) * v;
+        j[1] += cy<L>(i) * v;
+        j[2] += cz<L>(i) * v;
+      }
+    }
+    const double r = rr[n], b = rb[n], rho = r + b;
+    double F[3] = {a.body[0], a.body[1], a.body[2]};
+    if (!wall && a.model != LBM_MODEL_CG) {
+      const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+      double s1[3] = {0.0, 0.0, 0.0}, s2[3] = {0.0, 0.0, 0.0};
+      const double psic = a.rho0 * (1.0 - exp(-r / a.rho0));
+      for (int i = 1; i < L::Q; i++) {
+        const long long m = nb_index(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
+        const bool sw = solid && solid[m];
+        const double w = L::w(grp<L>(i));
+        if (a.model == LBM_MODEL_SC_MP) {
+          const double ps = sw ? psic : a.rho0 * (1.0 - exp(-rr[m] / a.rho0));
+          s1[0] += w * ps * cx<L>(i);
+          s1[1] += w * ps * cy<L>(i);
+          s1[2] += w * ps * cz<L>(i);
+        } else {
+          const double v2 = sw ? b : rb[m], v1 = sw ? r : rr[m];
+          s1[0] += w * v2 * cx<L>(i);
+          s1[1] += w * v2 * cy<L>(i);
+          s1[2] += w * v2 * cz<L>(i);
+          s2[0] += w * v1 * cx<L>(i);
+          s2[1] += w * v1 * cy<L>(i);
+          s2[2] += w * v1 * cz<L>(i);
+        }
+      }
+      for (int dd = 0; dd < 3; dd++) {
+        if (a.model == LBM_MODEL_SC_MP)
+          F[dd] = -a.G * psic * s1[dd] + a.body[dd];
+        else
+          F[dd] = -a.G * r * s1[dd] - a.G * b * s2[dd] + a.body[dd];
+      }
+    }
+    double u[3] = {0.0, 0.0, 0.0};
+    if (!wall)
+      for (int dd = 0; dd < 3; dd++) u[dd] = (j[dd] + 0.5 * F[dd]) / rho;
+    if (uo) {
+      uo[n] = u[0];
+      uo[a.n + n] = u[1];
+      uo[2 * a.n + n] = u[2];
+    }
+    if (wall) continue;
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    acc.v[0] += r;
+    acc.v[1] += b;
+    acc.v[2] += j[0];
+    acc.v[3] += j[1];
+    acc.v[4] += j[2];
+    acc.v[5] += 0.5 * rho * uu;
+    acc.v[6] = fmax(acc.v[6], sqrt(uu));
+    acc.v[7] += bad;
+    acc.v[8] = fmin(acc.v[8], r);
+    acc.v[9] = fmin(acc.v[9], b);
+  }
+  block_reduce(acc);
+  if (threadIdx.x == 0)
+    for (int s = 0; s < LBM_NTOTALS; s++) partials[blockIdx.x * LBM_NTOTALS + s] = acc.v[s];
+}
+
+__global__ void __launch_bounds__(kDiagThreads) finalize_kernel(const double* __restrict__ partials, int nblk,
+                                                                lbm_diag* __restrict__ d, int cur, AuxParams a) {
+  Acc acc;
+  acc_init(acc);
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    Acc o;
+    for (int s = 0; s < LBM_NTOTALS; s++) o.v[s] = partials[b * LBM_NTOTALS + s];
+    acc_merge(acc, o);
+  }
+  block_reduce(acc);
+  if (threadIdx.x == 0) {
+    int st = 0;
+    if (acc.v[7] > 0 || !isfinite(acc.v[0]) || !isfinite(acc.v[1])) st |= 1;
+    if (acc.v[8] < -a.neg_tol || acc.v[9] < -a.neg_tol) st |= 2;
+    if (!(acc.v[6] <= a.umax)) st |= 4;
+    for (int s = 0; s < LBM_NTOTALS; s++) d->totals[s] = acc.v[s];
+    if (d->status == 0 && st != 0) d->trip_buf = cur;
+    d->status |= st;
+  }
+}
+
+int grid_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <class L, class S, class RT>
+cudaError_t init_t(lbm_ctx* c, const double* rr, const double* rb, const double* u) {
+  const AuxParams a = aux_params(c);
+  init_eq_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
+      static_cast<S*>(c->f[0]), static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]), static_cast<RT*>(c->r[1]), rr,
+      rb, u, c->has_walls ? c->solid : nullptr, a);
+  return cudaGetLastError();
+}
+
+template <class L, class S, class RT>
+cudaError_t restore_t(lbm_ctx* c, const double* plane, int k, int i, const double* acc) {
+  double phi[2][3];
+  rest_weights(c->p, phi);
+  restore_plane_kernel<S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
+      static_cast<S*>(c->f[0]), static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]), static_cast<RT*>(c->r[1]),
+      plane, acc + (long long)k * c->N, c->has_walls ? c->solid : nullptr, c->N, (long long)(k * c->Q + i) * c->N,
+      (long long)k * c->N, phi[k][grp<L>(i)], i == 0);
+  return cudaGetLastError();
+}
+
+template <class L, class S, class RT>
+cudaError_t export_t(lbm_ctx* c, double* out, int first_plane, int np) {
+  const AuxParams a = aux_params(c);
+  export_kernel<L, S, RT><<<grid_for((long long)np * c->N, 256, 16384), 256, 0, c->stream>>>(
+      static_cast<const S*>(c->f[0]), static_cast<const S*>(c->f[1]), static_cast<const RT*>(c->r[0]),
+      static_cast<const RT*>(c->r[1]), c->diag, c->cur, first_plane, np, out, a);
+  return cudaGetLastError();
+}
+
+template <class L, class S, class RT>
+cudaError_t diag_t(lbm_ctx* c, double* uo) {
+  const AuxParams a = aux_params(c);
+  const S* f0 = static_cast<const S*>(c->f[0]);
+  const S* f1 = static_cast<const S*>(c->f[1]);
+  const RT* r0 = static_cast<const RT*>(c->r[0]);
+  const RT* r1 = static_cast<const RT*>(c->r[1]);
+  double* rr = c->stage;
+  double* rb = c->stage + c->N;
+  densities_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(f0, f1, r0, r1, c->diag, c->cur, rr,
+                                                                               rb, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_kernel<L, S, RT><<<c->nblk_diag, kDiagThreads, 0, c->stream>>>(f0, f1, r0, r1, c->diag, c->cur, rr, rb,
+                                                                       c->has_walls ? c->solid : nullptr, uo,
+                                                                       c->partials, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finalize_kernel<<<1, kDiagThreads, 0, c->stream>>>(c->partials, c->nblk_diag, c->diag, c->cur, a);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
+// Dispatch on (lattice, storage precision) to an operation templated on <L, S, RT>.
+template <template <class, class, class> class F, class... Args>
+cudaError_t by_lattice_precision(lbm_ctx* c, Args... args) {
+  const bool d3 = c->p.lattice == LBM_D3Q19;
+  switch (c->p.precision) {
+    case LBM_FP64:
+      return d3 ? F<D3Q19, double, double>::run(c, args...) : F<D2Q9, double, double>::run(c, args...);
+    case LBM_FP32:
+      return d3 ? F<D3Q19, float, float>::run(c, args...) : F<D2Q9, float, float>::run(c, args...);
+    case LBM_FP16:
+      return d3 ? F<D3Q19, __half, float>::run(c, args...) : F<D2Q9, __half, float>::run(c, args...);
+    default:
+      return d3 ? F<D3Q19, __nv_bfloat16, float>::run(c, args...) : F<D2Q9, __nv_bfloat16, float>::run(c, args...);
+  }
+}
+
+template <class L, class S, class RT>
+struct InitOp {
+  static cudaError_t run(lbm_ctx* c, const double* rr, const double* rb, const double* u) {
+    return init_t<L, S, RT>(c, rr, rb, u);
+  }
+};
+template <class L, class S, class RT>
+struct RestoreOp {
+  static cudaError_t run(lbm_ctx* c, const double* plane, int k, int i, const double* acc) {
+    return restore_t<L, S, RT>(c, plane, k, i, acc);
+  }
+};
+template <class L, class S, class RT>
+struct ExportOp {
+  static cudaError_t run(lbm_ctx* c, double* out, int first, int np) { return export_t<L, S, RT>(c, out, first, np); }
+};
+template <class L, class S, class RT>
+struct DiagOp {
+  static cudaError_t run(lbm_ctx* c, double* uo) { return diag_t<L, S, RT>(c, uo); }
+};
+
+}  // namespace
+
+cudaError_t launch_init_eq(lbm_ctx* c, const double* rr, const double* rb, const double* u) {
+  c->launches += 1;
+  return by_lattice_precision<InitOp>(c, rr, rb, u);
+}
+
+cudaError_t launch_restore_accumulate(lbm_ctx* c, const double* plane, int k, double* acc, bool first) {
+  c->launches += 1;
+  restore_acc_kernel<<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(plane, acc + (long long)k * c->N, c->N, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore_plane(lbm_ctx* c, const double* plane, int k, int i, const double* acc) {
+  c->launches += 1;
+  return by_lattice_precision<RestoreOp>(c, plane, k, i, acc);
+}
+
+cudaError_t launch_export_plane(lbm_ctx* c, double* plane, int k, int i) {
+  c->launches += 1;
+  return by_lattice_precision<ExportOp>(c, plane, k * c->Q + i, 1);
+}
+
+cudaError_t launch_export_all(lbm_ctx* c, double* pops) {
+  c->launches += 1;
+  return by_lattice_precision<ExportOp>(c, pops, 0, c->K * c->Q);
+}
+
+cudaError_t launch_diagnostics(lbm_ctx* c, double* u_out, bool want_u) {
+  double* uo = u_out ? u_out : (want_u ? c->stage + 2 * c->N : nullptr);
+  return by_lattice_precision<DiagOp>(c, uo);
+}
+
+}  // namespace lbm

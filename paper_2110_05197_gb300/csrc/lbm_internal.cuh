@@ -1,0 +1,124 @@
+// Host-side context and launcher declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/lbm.h"
+#include "lbm_step.cuh"
+
+// Device-side diagnostics record: totals (LBM_NTOTALS doubles) then the blow-up status.
+struct lbm_diag {
+  double totals[LBM_NTOTALS];
+  int status;       // 0 ok; bit 0 non-finite, bit 1 negative density, bit 2 |u| too large
+  int trip_buf;     // population buffer (0/1) holding the state the check tripped on; after a
+                    // trip the step kernels write nothing, so that buffer stays the state
+  int pad[2];
+};
+
+struct lbm_ctx {
+  lbm_params p;
+  int K, Q;
+  long long N;
+  size_t elt;            // bytes per stored population
+  size_t relt;           // bytes per reference density
+  cudaStream_t stream;
+  unsigned char* ws;
+  size_t ws_bytes;
+  void* f[2];            // A/B population buffers [K][Q][N], deviations from phi * r
+  void* r[2];            // A/B reference densities [K][N] (paired with f[])
+  int cur;               // index of the buffer pair holding the current state
+  uint8_t* solid;        // [N] wall mask (all zero without walls)
+  bool has_walls;
+  double* stage;         // [5][N] FP64 staging: rho_r, rho_b, u_x, u_y, u_z
+  double* partials;      // [nblk_diag][LBM_NTOTALS]
+  int nblk_diag;
+  lbm_diag* diag;        // device
+  bool initialised;
+  lbm_status sticky;
+  unsigned long long launches;
+  long long steps;
+  int tx, ty, tz;        // step kernel tiling
+};
+
+namespace lbm {
+
+constexpr int kDiagThreads = 256;
+
+// Workspace layout; returns the total size.  All regions 256-byte aligned.
+size_t workspace_layout(const lbm_params& p, lbm_ctx* c /* may be null: size only */);
+
+// Step launchers (one step: fin = f[cur] -> fout = f[cur^1]); return cudaSuccess or the
+// launch error.
+cudaError_t launch_step_f64(lbm_ctx* c);
+cudaError_t launch_step_f32(lbm_ctx* c);
+cudaError_t launch_step_f16(lbm_ctx* c);
+cudaError_t launch_step_bf16(lbm_ctx* c);
+size_t step_smem_for(const lbm_ctx* c, int tx, int ty);
+
+// Aux launchers (lbm_aux.cu)
+cudaError_t launch_init_eq(lbm_ctx* c, const double* rr, const double* rb, const double* u);
+// Checkpoint restore in two passes over the populations: accumulate the densities
+// (acc [K][N] FP64), then write deviations relative to them.
+cudaError_t launch_restore_accumulate(lbm_ctx* c, const double* plane, int k, double* acc, bool first);
+cudaError_t launch_restore_plane(lbm_ctx* c, const double* plane, int k, int i, const double* acc);
+cudaError_t launch_export_plane(lbm_ctx* c, double* plane, int k, int i);
+cudaError_t launch_export_all(lbm_ctx* c, double* pops);
+// Densities into stage[0..2N), velocity into u_out (or stage[2N..5N) when null and
+// want_u), block partials, then the fixed-order final reduction into c->diag.
+cudaError_t launch_diagnostics(lbm_ctx* c, double* u_out, bool want_u);
+
+// Rest-state equilibrium weights per component and group: Eq. phi with alpha_k for CG
+// (alpha_R from Eq. gamma), the lattice weights w for SC.
+inline void rest_weights(const lbm_params& q, double phi[2][3]) {
+  const bool d3 = q.lattice == LBM_D3Q19;
+  for (int k = 0; k < 2; k++) {
+    if (q.model == LBM_MODEL_CG) {
+      const double alpha = k == 0 ? 1.0 - (1.0 - q.alpha_b) * q.rho_b0 / q.rho_r0 : q.alpha_b;
+      phi[k][0] = alpha;
+      phi[k][1] = (d3 ? D3Q19::phi_num(1) : D2Q9::phi_num(1)) * (1.0 - alpha);
+      phi[k][2] = (d3 ? D3Q19::phi_num(2) : D2Q9::phi_num(2)) * (1.0 - alpha);
+    } else {
+      for (int g = 0; g < 3; g++) phi[k][g] = d3 ? D3Q19::w(g) : D2Q9::w(g);
+    }
+  }
+}
+
+template <class T>
+StepParams<T> make_step_params(const lbm_ctx* c) {
+  const lbm_params& q = c->p;
+  StepParams<T> s{};
+  s.nx = q.nx;
+  s.ny = q.ny;
+  s.nz = q.nz;
+  s.tz = c->tz;
+  s.n = c->N;
+  double phi[2][3];
+  rest_weights(q, phi);
+  for (int k = 0; k < 2; k++)
+    for (int g = 0; g < 3; g++) s.phi[k][g] = T(phi[k][g]);
+  s.inv_nu_r = T(3.0 / (q.tau_r - 0.5));
+  s.inv_nu_b = T(3.0 / (q.tau_b - 0.5));
+  s.A = T(q.A);
+  s.beta = T(q.beta);
+  s.grad_eps = T(q.grad_eps);
+  s.inv_rho_r0 = T(1.0 / q.rho_r0);
+  s.inv_rho_b0 = T(1.0 / q.rho_b0);
+  s.enhanced = q.enhanced_eq;
+  s.color_norm = q.color_norm;
+  if (q.model == LBM_MODEL_SC_2C)
+    s.G = T(q.G / (q.rho0_psi * q.rho0_psi));
+  else
+    s.G = T(q.G);
+  s.rho0 = T(q.rho0_psi);
+  s.inv_rho0 = T(1.0 / q.rho0_psi);
+  s.omega_r = T(1.0 / q.tau_r);
+  s.omega_b = T(1.0 / q.tau_b);
+  for (int a = 0; a < 3; a++) s.body[a] = T(q.body_force[a]);
+  s.has_body = (q.body_force[0] != 0.0 || q.body_force[1] != 0.0 || q.body_force[2] != 0.0);
+  return s;
+}
+
+}  // namespace lbm

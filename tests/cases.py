@@ -1,0 +1,108 @@
+"""Seeded parity cases shared by the GPU tests: each yields the parameters for both sides
+and the initial fields from the input generators (geometry and noise only)."""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from paper_2110_05197_gb300 import inputs
+
+# SC multiphase coexistence at G = -5 (mechanical stability with Guo forcing)
+SC_LIQ, SC_GAS = 1.8884, 0.1194
+
+
+@dataclass
+class Case:
+    name: str
+    kw: dict                    # shared parameters (oracle.Params / lbm.Params field names)
+    rho_r: np.ndarray
+    rho_b: np.ndarray | None = None
+    u: np.ndarray | None = None
+    solid: np.ndarray | None = None
+
+
+def cg_drop3d(nx=20, ny=18, nz=17, ratio=10.0, seed=2, **extra):
+    rr, rb = inputs.two_fluid(inputs.ellipsoid(nx, ny, nz, (7, 6, 5)), 1.0, 1.0 / ratio, 0.01, seed)
+    kw = dict(lattice=1, model=0, nx=nx, ny=ny, nz=nz, rho_r0=1.0, rho_b0=1.0 / ratio, tau_r=1.0, tau_b=0.7,
+              A=5e-3)
+    kw.update(extra)
+    return Case("cg_drop3d", kw, rr, rb)
+
+
+def cg_drop2d(n=40, seed=1, **extra):
+    rr, rb = inputs.two_fluid(inputs.sphere(n, n + 3, 1, 10), 1.0, 1.0, 0.0, seed)
+    kw = dict(lattice=0, model=0, nx=n, ny=n + 3, nz=1, rho_r0=1.0, rho_b0=1.0, A=1e-2)
+    kw.update(extra)
+    return Case("cg_drop2d", kw, rr, rb)
+
+
+def cg_walls3d(nx=12, ny=14, nz=10, **extra):
+    solid = inputs.channel_walls(nx, ny, nz)
+    ins = inputs.sphere(nx, ny, nz, 4.0)
+    rr, rb = inputs.two_fluid(ins, 1.0, 0.5, 0.01, 5)
+    rr = np.where(solid, 0.0, rr)
+    rb = np.where(solid, 0.0, rb)
+    kw = dict(lattice=1, model=0, nx=nx, ny=ny, nz=nz, rho_r0=1.0, rho_b0=0.5, tau_r=0.9, tau_b=0.6, A=4e-3,
+              body_force=(1e-5, 0.0, 2e-6))
+    kw.update(extra)
+    return Case("cg_walls3d", kw, rr, rb, None, solid)
+
+
+def sc_mp3d(nx=20, ny=18, nz=17, seed=3, **extra):
+    ins = inputs.sphere(nx, ny, nz, 5.5)
+    rho = np.where(ins, SC_LIQ, SC_GAS) * (1 + 0.01 * inputs.uniform_pm1(seed, nx * ny * nz))
+    kw = dict(lattice=1, model=1, nx=nx, ny=ny, nz=nz, G=-5.0, rho0_psi=1.0, tau_r=1.0)
+    kw.update(extra)
+    return Case("sc_mp3d", kw, rho)
+
+
+def sc_2c3d(nx=20, ny=18, nz=17, seed=4, **extra):
+    rr, rb = inputs.two_fluid(inputs.sphere(nx, ny, nz, 5.5), 1.0, 1.0, 0.01, seed)
+    kw = dict(lattice=1, model=2, nx=nx, ny=ny, nz=nz, G=0.9, rho0_psi=0.577, tau_r=1.0, tau_b=0.8)
+    kw.update(extra)
+    return Case("sc_2c3d", kw, rr + 0.03, rb + 0.03)
+
+
+def sc_walls2d(nx=24, ny=20, **extra):
+    solid = inputs.channel_walls(nx, ny, 1)
+    ins = inputs.sphere(nx, ny, 1, 5.0)
+    rho = np.where(ins, SC_LIQ, SC_GAS)
+    rho = np.where(solid, 0.0, rho)
+    kw = dict(lattice=0, model=1, nx=nx, ny=ny, nz=1, G=-5.0, rho0_psi=1.0, tau_r=0.9,
+              body_force=(2e-6, 0.0, 0.0))
+    kw.update(extra)
+    return Case("sc_walls2d", kw, rho, None, None, solid)
+
+
+SMALL_CASES = {
+    "cg_drop3d": cg_drop3d,
+    "cg_drop2d": cg_drop2d,
+    "cg_walls3d": cg_walls3d,
+    "cg_std_norm": lambda: cg_drop3d(enhanced_eq=0, color_norm=1, ratio=4.0),
+    "sc_mp3d": sc_mp3d,
+    "sc_2c3d": sc_2c3d,
+    "sc_walls2d": sc_walls2d,
+}
+
+
+def oracle_sim(orc, case: Case, threads: int | None = None):
+    if threads:
+        orc.set_threads(threads)
+    s = orc.OracleSim(orc.Params(**case.kw))
+    s.init(case.rho_r, case.rho_b, case.u, case.solid)
+    return s
+
+
+def gpu_lattice(lbm, case: Case, precision: int, **extra):
+    import torch
+    kw = dict(case.kw)
+    kw.update(extra)
+    lat = lbm.Lattice(lbm.Params(precision=precision, **kw))
+    dev = lat.device
+
+    def t(a, dt=torch.float64):
+        return None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+
+    lat.init(t(case.rho_r), t(case.rho_b), t(case.u), t(case.solid, torch.uint8))
+    return lat

@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads and exports every entry point include/*.h declares; the
+size query and argument validation work without a GPU (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2110_05197_gb300 import build as lbm_build
+from paper_2110_05197_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    lbm_build.build()
+    return lbm.lib()
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("lbm_create", "lbm_init_fields", "lbm_step_cg", "lbm_step_sc", "lbm_moments",
+                     "lbm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared_functions()
+    assert names
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in lbm.SIGNATURES, f"binding lacks {n}"
+
+
+def _size(L, **kw):
+    p = lbm.Params(**kw).to_c()
+    need = ctypes.c_size_t(0)
+    rc = L.lbm_create(ctypes.byref(p), None, ctypes.byref(need), None, None)
+    return rc, need.value
+
+
+def test_workspace_size_query(L):
+    rc, b = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP32, model=lbm.CG)
+    assert rc == lbm.OK
+    N = 128 ** 3
+    pops = 2 * 2 * 19 * N * 4   # A/B populations
+    ref = 2 * 2 * N * 4         # A/B reference densities
+    assert pops + ref < b < pops + ref + 5 * N * 8 + 2 * N + (1 << 20)
+    rc, b64 = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP64, model=lbm.CG)
+    assert b64 - b == 2 * 2 * 19 * N * 4 + ref
+    rc, b16 = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP16, model=lbm.CG)
+    assert b - b16 == 2 * 2 * 19 * N * 2
+    rc, bsc = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP32, model=lbm.SC_MP)
+    assert b - bsc == 2 * 19 * N * 4 + 2 * N * 4
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=0), dict(lattice=lbm.D2Q9, nz=4), dict(tau_r=0.5), dict(precision=4), dict(model=9),
+    dict(rho_b0=-1.0), dict(model=lbm.SC_MP, rho0_psi=0.0), dict(diag_every=-1),
+    dict(rho_r0=0.1, rho_b0=1.0),  # alpha_R < 0 from Eq. gamma
+])
+def test_invalid_parameters_rejected(L, bad):
+    rc, _ = _size(L, **bad)
+    assert rc == lbm.EINVAL
+
+
+def test_status_strings(L):
+    for s in range(7):
+        assert L.lbm_status_string(s)
+    assert L.lbm_destroy(None) == lbm.OK
+    assert L.lbm_launch_count(None) == 0
+    assert L.lbm_step_cg(None, 1) == lbm.EINVAL
+    assert L.lbm_moments(None, None, None, None, None, None) == lbm.EINVAL
