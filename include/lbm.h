@@ -165,6 +165,28 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, const uint8_t* solid);
 
+/* Allocation-free totals (the paper has no counterpart; this serves callers that cannot
+ * call cudaMalloc, e.g. a plugin whose host application's caching allocator has reserved
+ * the device memory, or a loop that must never enter the driver's allocation path).
+ * Computes the LBM_NTOTALS totals lbm_moments reports (same definitions, FP64, fixed-order
+ * reduction) from caller-owned canonical populations, without a context or workspace.
+ *   p      : lattice, model, nx/ny/nz and the force parameters (G, rho0_psi, body_force,
+ *            rho_r0/rho_b0, umax_unstable) of the state; precision is ignored.
+ *   pops   : DEVICE pointer, FP64 canonical populations [K][Q][N] (as lbm_moments exports).
+ *   solid  : DEVICE pointer to the uint8 wall mask [N], or NULL.
+ *   totals : host or device pointer to LBM_NTOTALS doubles (written).
+ *   stream : cudaStream_t the work is enqueued on; the call synchronises it.
+ * Scratch lives in one static __device__ array of 16 MiB + 96 KiB per device that loads
+ * the library, held until process exit; nothing is allocated by the call.  The first call
+ * on a device looks up that array's address (cudaGetSymbolAddress, with the caller's
+ * device current) and so should come before any stream capture on that device.  Calls
+ * share the array: calls that overlap on the GPU race and must be serialised.
+ * Errors: LBM_EINVAL for NULL/host pops, N > LBM_NOALLOC_MAX_NODES or bad sizes;
+ * LBM_ECUDA on a CUDA error; LBM_EUNSTABLE when the blow-up check trips (totals written). */
+enum { LBM_NOALLOC_MAX_NODES = 1 << 20 };
+lbm_status lbm_totals_noalloc(const lbm_params* p, const double* pops, const uint8_t* solid, double* totals,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

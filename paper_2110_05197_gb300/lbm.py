@@ -66,7 +66,22 @@ SIGNATURES = {
     "lbm_state_bytes": (ctypes.c_size_t, [_VP]),
     "lbm_save_state": (ctypes.c_int, [_VP, _VP]),
     "lbm_load_state": (ctypes.c_int, [_VP, _VP, _VP]),
+    "lbm_totals_noalloc": (ctypes.c_int, [ctypes.POINTER(_CParams), _VP, _VP, _VP, _VP]),
 }
+NOALLOC_MAX_NODES = 1 << 20
+
+
+def totals_noalloc(params: "Params", pops, solid=None, out=None, stream=None):
+    """lbm_totals_noalloc: totals of caller-owned canonical FP64 populations on the device,
+    using the library's static scratch (no allocation).  Returns (totals, status)."""
+    cp = params.to_c()
+    if out is None:
+        out = np.zeros(NTOTALS)
+    s = stream.cuda_stream if stream is not None else None
+    rc = lib().lbm_totals_noalloc(ctypes.byref(cp), _ptr(pops), _ptr(solid), _ptr(out), s)
+    if rc not in (OK, EUNSTABLE):
+        raise LbmError(rc, "lbm_totals_noalloc")
+    return out, rc
 
 _lib = None
 
