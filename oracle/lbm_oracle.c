@@ -29,7 +29,8 @@
  *   - phi_i^k (Eq. phi) is used in the BGK equilibrium too (with phi=0 the BGK step would
  *     not conserve mass); f^eq|_{u=0} in the recolouring is sum_k rho_k phi_i^k.
  *   - Both colours relax with the local omega_eff; nu_k = (tau_k - 1/2)/3.
- *   - Gradients: isotropic finite difference grad phi = 3 sum_i w_i phi(x+c_i) c_i.
+ *   - Gradients: isotropic finite difference grad phi = 3 sum_i w_i phi(x+c_i) c_i, summed
+ *     as opposite-pair differences.
  *   - Forces enter CG through Guo forcing with tau = 1/omega_eff, on the total population.
  *   - Walls: halfway bounce-back; a solid neighbour's scalar is replaced by the centre's.
  *   - psi_rep defaults to (1-|rho^N|)^chi (maximal at rho^N = 0, decaying away from it);
@@ -286,13 +287,19 @@ void orc_destroy(orc_sim* s) {
   free(s);
 }
 
-/* grad phi(x) = 3 sum_i w_i phi(x + c_i) c_i; a solid neighbour contributes phi(x). */
+/* grad phi(x) = 3 sum_i w_i phi(x + c_i) c_i, summed over opposite pairs as
+ * 3 w_i (phi(x + c_i) - phi(x - c_i)) c_i so that a field constant along a lattice direction
+ * gives an exactly zero component (the Heaviside factor of Eq. repForce is then decided on
+ * exact zeros, not rounding residues); a solid neighbour contributes phi(x). */
 static void gradient(const orc_sim* s, const double* phi, size_t n, double* g) {
   g[0] = g[1] = g[2] = 0.0;
   for (int i = 1; i < s->L.q; i++) {
-    size_t m = neighbour(s, n, i);
-    double v = s->solid[m] ? phi[n] : phi[m];
-    for (int a = 0; a < 3; a++) g[a] += 3.0 * s->L.w[i] * v * s->L.c[i][a];
+    int j = s->L.opp[i];
+    if (j < i) continue;
+    size_t mp = neighbour(s, n, i), mm = neighbour(s, n, j);
+    double vp = s->solid[mp] ? phi[n] : phi[mp];
+    double vm = s->solid[mm] ? phi[n] : phi[mm];
+    for (int a = 0; a < 3; a++) g[a] += 3.0 * s->L.w[i] * (vp - vm) * s->L.c[i][a];
   }
 }
 
