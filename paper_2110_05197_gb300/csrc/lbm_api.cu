@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <cudaTypedefs.h>
+
 #include "lbm_internal.cuh"
 
 namespace {
@@ -93,6 +95,10 @@ size_t workspace_layout(const lbm_params& p, lbm_ctx* c) {
   const size_t ostg = take((size_t)5 * N * sizeof(double));
   const size_t opar = take((size_t)nblk * LBM_NTOTALS * sizeof(double));
   const size_t odia = take(sizeof(lbm_diag));
+  const bool rep = p.model == LBM_MODEL_CG && p.rep_pi != 0.0;
+  const size_t tsz = p.precision == LBM_FP64 ? 8 : 4;  // step compute type
+  const size_t ocol = rep ? take((size_t)N * tsz) : 0;
+  const size_t onrm = rep ? take((size_t)3 * N * tsz) : 0;
   if (c) {
     c->K = K;
     c->Q = Q;
@@ -108,6 +114,9 @@ size_t workspace_layout(const lbm_params& p, lbm_ctx* c) {
     c->partials = reinterpret_cast<double*>(c->ws + opar);
     c->nblk_diag = nblk;
     c->diag = reinterpret_cast<lbm_diag*>(c->ws + odia);
+    c->rep = rep;
+    c->colour = rep ? c->ws + ocol : nullptr;
+    c->normals = rep ? c->ws + onrm : nullptr;
   }
   return off;
 }
@@ -127,6 +136,66 @@ static cudaError_t launch_step(lbm_ctx* c) {
     case LBM_FP16: return launch_step_f16(c);
     default: return launch_step_bf16(c);
   }
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+static EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 4-D view (x, array, y, z) of a [arrays][z][y][x] buffer with boxes {bx, arrays, rows, 1}.
+static bool encode4(EncodeFn fn, CUtensorMap* m, CUtensorMapDataType dt, size_t elt, void* base, int nx, int ny,
+                    int nz, int arrays, long long n, int bx, int rows) {
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)arrays, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[3] = {(cuuint64_t)(n * elt), (cuuint64_t)nx * elt, (cuuint64_t)nx * ny * elt};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)arrays, (cuuint32_t)rows, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool build_tma_maps(lbm_ctx* c) {
+  const lbm_params& p = c->p;
+  if (p.lattice != LBM_D3Q19 || p.precision == LBM_FP64) return false;
+  if (p.nx % kTmaTX != 0 || p.ny % kTmaTY != 0) return false;
+  const int K = c->K, Q = c->Q;
+  if (K * Q > 256) return false;
+  EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  const CUtensorMapDataType dt = p.precision == LBM_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : p.precision == LBM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const int sw = (int)(16 / c->elt), rsw = (int)(16 / c->relt);
+  for (int b = 0; b < 2; b++) {
+    TmaMaps& m = c->tma[b];
+    bool ok = encode4(fn, &m.pop_main_row, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, kTmaTX, 1) &&
+              encode4(fn, &m.pop_main_mid, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, kTmaTX, kTmaTY) &&
+              encode4(fn, &m.pop_strip_row, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, sw, 1) &&
+              encode4(fn, &m.pop_strip_mid, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, sw, kTmaTY) &&
+              encode4(fn, &m.ref_main_row, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
+                      c->N, kTmaTX, 1) &&
+              encode4(fn, &m.ref_main_mid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
+                      c->N, kTmaTX, kTmaTY) &&
+              encode4(fn, &m.ref_strip_row, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
+                      c->N, rsw, 1) &&
+              encode4(fn, &m.ref_strip_mid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
+                      c->N, rsw, kTmaTY);
+    if (!ok) return false;
+  }
+  return true;
 }
 
 }  // namespace lbm
@@ -172,6 +241,7 @@ lbm_status lbm_create(const lbm_params* p, void* ws, size_t* ws_bytes, void* str
   c->tx = 32;
   c->ty = 8;
   c->tz = p->lattice == LBM_D3Q19 ? (p->nz < 16 ? p->nz : 16) : 1;
+  c->tma_ok = lbm::build_tma_maps(c);
   *out = c;
   return LBM_OK;
 }
@@ -320,6 +390,7 @@ lbm_status lbm_moments(lbm_ctx* c, double* rho_r, double* rho_b, double* u, doub
   }
   if (totals) {
     std::memcpy(totals, hd.totals, sizeof(hd.totals));
+    if (hd.status & (lbm::kStatusTimeout | lbm::kStatusLayout)) return LBM_ETIMEOUT;
     if (hd.status != 0) return LBM_EUNSTABLE;
   }
   return LBM_OK;

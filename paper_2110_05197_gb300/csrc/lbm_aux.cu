@@ -5,8 +5,9 @@
 // equilibrium of a per-node reference density r_k (see lbm_step.cuh); every kernel here
 // reconstructs f in FP64 as g + phi r.
 #include <cmath>
+#include <type_traits>
 
-#include "lbm_internal.cuh"
+#include "lbm_launch.cuh"
 
 namespace lbm {
 
@@ -252,6 +253,10 @@ __device__ void block_reduce(Acc& a) {
   }
 }
 
+// compute type of the step for a storage type (the repulsion pre-pass fields use it)
+template <class S>
+using step_t = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+
 template <class L, class S, class RT>
 __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict__ f0, const S* __restrict__ f1,
                                                             const RT* __restrict__ r0, const RT* __restrict__ r1,
@@ -259,7 +264,9 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
                                                             const double* __restrict__ rr,
                                                             const double* __restrict__ rb,
                                                             const uint8_t* __restrict__ solid, double* __restrict__ uo,
-                                                            double* __restrict__ partials, AuxParams a) {
+                                                            double* __restrict__ partials, AuxParams a,
+                                                            const step_t<S>* __restrict__ colour,
+                                                            const step_t<S>* __restrict__ normals, RepParams rp) {
   const int bsel = state_index(d, cur);
   const S* f = bsel ? f1 : f0;
   const RT* rref = bsel ? r1 : r0;
@@ -283,6 +290,12 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
     }
     const double r = rr[n], b = rb[n], rho = r + b;
     double F[3] = {a.body[0], a.body[1], a.body[2]};
+    if (!wall && a.model == LBM_MODEL_CG && normals) {
+      const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+      step_t<S> Fr[3];
+      rep_force<L, step_t<S>>(normals, colour, solid, x, y, z, rp, Fr);
+      for (int dd = 0; dd < 3; dd++) F[dd] += (double)Fr[dd];
+    }
     if (!wall && a.model != LBM_MODEL_CG) {
       const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
       double s1[3] = {0.0, 0.0, 0.0}, s2[3] = {0.0, 0.0, 0.0};
@@ -409,9 +422,13 @@ cudaError_t diag_t(lbm_ctx* c, double* uo) {
                                                                                rb, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  diag_kernel<L, S, RT><<<c->nblk_diag, kDiagThreads, 0, c->stream>>>(f0, f1, r0, r1, c->diag, c->cur, rr, rb,
-                                                                       c->has_walls ? c->solid : nullptr, uo,
-                                                                       c->partials, a);
+  if (c->rep) {
+    e = launch_rep_prepass_t<L, step_t<S>, S, RT>(c, c->cur);
+    if (e != cudaSuccess) return e;
+  }
+  diag_kernel<L, S, RT><<<c->nblk_diag, kDiagThreads, 0, c->stream>>>(
+      f0, f1, r0, r1, c->diag, c->cur, rr, rb, c->has_walls ? c->solid : nullptr, uo, c->partials, a,
+      static_cast<const step_t<S>*>(c->colour), static_cast<const step_t<S>*>(c->normals), rep_params(c));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   finalize_kernel<<<1, kDiagThreads, 0, c->stream>>>(c->partials, c->nblk_diag, c->diag, c->cur, a);

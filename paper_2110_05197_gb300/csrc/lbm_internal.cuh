@@ -8,6 +8,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_step.cuh"
+#include "lbm_step_tma.cuh"
 
 // Device-side diagnostics record: totals (LBM_NTOTALS doubles) then the blow-up status.
 struct lbm_diag {
@@ -41,6 +42,11 @@ struct lbm_ctx {
   unsigned long long launches;
   long long steps;
   int tx, ty, tz;        // step kernel tiling
+  bool rep;              // CG repulsion force enabled (rep_pi != 0)
+  void* colour;          // [N] rho^N (step compute type), repulsion pre-pass
+  void* normals;         // [3][N] unit colour gradients, repulsion pre-pass
+  bool tma_ok;           // tensor maps built: the TMA-staged kernel can run this lattice
+  lbm::TmaMaps tma[2];   // maps for reading buffer pair 0 / 1
 };
 
 namespace lbm {
@@ -57,6 +63,9 @@ cudaError_t launch_step_f32(lbm_ctx* c);
 cudaError_t launch_step_f16(lbm_ctx* c);
 cudaError_t launch_step_bf16(lbm_ctx* c);
 size_t step_smem_for(const lbm_ctx* c, int tx, int ty);
+// Encode the tensor maps of both buffer pairs when the lattice suits the TMA-staged
+// kernel (D3Q19, FP32/FP16/BF16 storage, nx % 32 == 0, ny % 8 == 0); false otherwise.
+bool build_tma_maps(lbm_ctx* c);
 
 // Aux launchers (lbm_aux.cu)
 cudaError_t launch_init_eq(lbm_ctx* c, const double* rr, const double* rb, const double* u);
@@ -69,6 +78,8 @@ cudaError_t launch_export_all(lbm_ctx* c, double* pops);
 // Densities into stage[0..2N), velocity into u_out (or stage[2N..5N) when null and
 // want_u), block partials, then the fixed-order final reduction into c->diag.
 cudaError_t launch_diagnostics(lbm_ctx* c, double* u_out, bool want_u);
+// Repulsion pre-pass (colour and normal fields) of the current state, for the diagnostics.
+cudaError_t launch_rep_prepass(lbm_ctx* c);
 
 // Rest-state equilibrium weights per component and group: Eq. phi with alpha_k for CG
 // (alpha_R from Eq. gamma), the lattice weights w for SC.

@@ -2,17 +2,99 @@
 // precision, model and wall variant).
 #pragma once
 
+#include <algorithm>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
 
+// rho^N for the repulsion pre-pass, with the step's density bookkeeping
+template <class L, class T, class S, class RT>
+__global__ void colour_kernel(const S* __restrict__ f, const RT* __restrict__ r, T* __restrict__ colour,
+                              RepParams a) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+    T rho[2];
+    for (int k = 0; k < 2; k++) {
+      T g[L::Q];
+#pragma unroll
+      for (int i = 0; i < L::Q; i++) g[i] = ld_s<S, T>(f[(long long)(k * L::Q + i) * a.n + m]);
+      rho[k] = comp_state<L, T, RT>(g, T(r[(long long)k * a.n + m])).rho;
+    }
+    T s0 = rho[0], s1 = rho[1];
+    if (a.color_norm) {
+      s0 = s0 * T(a.inv_rho_r0);
+      s1 = s1 * T(a.inv_rho_b0);
+    }
+    colour[m] = (s0 - s1) / (s0 + s1);
+  }
+}
+
+
+inline RepParams rep_params(const lbm_ctx* c) {
+  RepParams a{};
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.nz = c->p.nz;
+  a.n = c->N;
+  a.color_norm = c->p.color_norm;
+  a.psi_kind = c->p.rep_psi_kind;
+  a.inv_rho_r0 = 1.0 / c->p.rho_r0;
+  a.inv_rho_b0 = 1.0 / c->p.rho_b0;
+  a.grad_eps = c->p.grad_eps;
+  a.pi = c->p.rep_pi;
+  a.chi = c->p.rep_chi;
+  return a;
+}
+
+// Colour and normal fields of the current state (repulsion pre-pass).
+template <class L, class T, class S, class RT>
+cudaError_t launch_rep_prepass_t(lbm_ctx* c, int buf) {
+  const RepParams a = rep_params(c);
+  const int grid = (int)std::min<long long>((c->N + 255) / 256, 8192);
+  colour_kernel<L, T, S, RT><<<grid, 256, 0, c->stream>>>(static_cast<const S*>(c->f[buf]),
+                                                           static_cast<const RT*>(c->r[buf]),
+                                                           static_cast<T*>(c->colour), a);
+  normals_kernel<L, T><<<grid, 256, 0, c->stream>>>(static_cast<const T*>(c->colour),
+                                                    c->has_walls ? c->solid : nullptr, static_cast<T*>(c->normals), a);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
 template <class L, class T, class S, class RT, int MODEL, bool WALLS>
+cudaError_t launch_tma_t(lbm_ctx* c) {
+  constexpr int TX = kTmaTX, TY = kTmaTY;
+  constexpr size_t smem = tma_smem_bytes<L, T, S, RT, MODEL, WALLS, TX, TY>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_tma<L, T, S, RT, MODEL, WALLS, TX, TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 block(TX, TY, 1);
+  dim3 grid(c->p.nx / TX, c->p.ny / TY, (c->p.nz + c->tz - 1) / c->tz);
+  const StepParams<T> sp = make_step_params<T>(c);
+  S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
+  RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
+  step_kernel_tma<L, T, S, RT, MODEL, WALLS, TX, TY><<<grid, block, smem, c->stream>>>(
+      c->tma[c->cur], fout, rout, c->solid, &c->diag->status, sp);
+  return cudaGetLastError();
+}
+
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 cudaError_t launch_step_t(lbm_ctx* c) {
+  if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
+    if (c->tma_ok && c->tx == kTmaTX && c->ty == kTmaTY) return launch_tma_t<L, T, S, RT, MODEL, WALLS>(c);
+  }
+  if constexpr (REP) {
+    cudaError_t e = launch_rep_prepass_t<L, T, S, RT>(c, c->cur);
+    if (e != cudaSuccess) return e;
+  }
   const int tx = c->tx, ty = c->ty;
   const size_t smem = step_smem_bytes<L, T, MODEL, WALLS>(tx, ty);
   static size_t smem_set = 0;  // largest dynamic shared memory opted in so far
   if (smem > 48 * 1024 && smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<L, T, S, RT, MODEL, WALLS>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<L, T, S, RT, MODEL, WALLS, REP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     smem_set = smem;
@@ -24,17 +106,25 @@ cudaError_t launch_step_t(lbm_ctx* c) {
   S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
   const RT* rin = static_cast<const RT*>(c->r[c->cur]);
   RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
-  step_kernel<L, T, S, RT, MODEL, WALLS><<<grid, block, smem, c->stream>>>(fin, fout, rin, rout, c->solid,
-                                                                          &c->diag->status, sp);
+  step_kernel<L, T, S, RT, MODEL, WALLS, REP><<<grid, block, smem, c->stream>>>(
+      fin, fout, rin, rout, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour),
+      static_cast<const T*>(c->normals), rep_params(c));
   return cudaGetLastError();
+}
+
+template <class L, class T, class S, class RT, int MODEL>
+cudaError_t dispatch_walls(lbm_ctx* c) {
+  const bool w = c->has_walls;
+  if constexpr (MODEL == kCG) {
+    if (c->rep) return w ? launch_step_t<L, T, S, RT, MODEL, true, true>(c) : launch_step_t<L, T, S, RT, MODEL, false, true>(c);
+  }
+  return w ? launch_step_t<L, T, S, RT, MODEL, true, false>(c) : launch_step_t<L, T, S, RT, MODEL, false, false>(c);
 }
 
 template <class T, class S, class RT, int MODEL>
 cudaError_t dispatch_lattice(lbm_ctx* c) {
-  const bool w = c->has_walls;
-  if (c->p.lattice == LBM_D3Q19)
-    return w ? launch_step_t<D3Q19, T, S, RT, MODEL, true>(c) : launch_step_t<D3Q19, T, S, RT, MODEL, false>(c);
-  return w ? launch_step_t<D2Q9, T, S, RT, MODEL, true>(c) : launch_step_t<D2Q9, T, S, RT, MODEL, false>(c);
+  if (c->p.lattice == LBM_D3Q19) return dispatch_walls<D3Q19, T, S, RT, MODEL>(c);
+  return dispatch_walls<D2Q9, T, S, RT, MODEL>(c);
 }
 
 template <class T, class S, class RT>

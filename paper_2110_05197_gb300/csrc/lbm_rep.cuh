@@ -1,0 +1,97 @@
+// Colour-gradient repulsion force (Sec. 2.3, Eqs. repForce, potential, normal1, normal2).
+//
+//   F_rep(x) = Pi psi_rep(rho^N(x)) sum_{i>=1} H(-(n.c_i)(n'_i.c_i)) [(n.c_i) n + (n'_i.c_i) n'_i] / |c_i|
+//
+// with n the unit colour gradient at x and n'_i the one at x + c_i.  The force needs the
+// colour gradient one node away, i.e. rho^N two nodes away, so it is computed from two
+// pre-pass fields written before each step that has it enabled:
+//   colour_kernel : rho^N(x) from the stored populations (the same density bookkeeping as
+//                   the step kernel);
+//   normals_kernel: n(x) = grad rho^N / |grad rho^N| (zero vector where |grad rho^N| <= eps,
+//                   which then contributes nothing), gradient by the isotropic stencil.
+// Readings: psi_rep = (1 - |rho^N|)^chi (or the printed (1 + |rho^N|)^chi), H(0) = 0,
+// direction 0 skipped, a wall neighbour contributes nothing.
+#pragma once
+
+#include <cstdint>
+
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+template <class T>
+__device__ __forceinline__ T fpow(T b, T e);
+template <>
+__device__ __forceinline__ float fpow<float>(float b, float e) { return e == 2.0f ? b * b : powf(b, e); }
+template <>
+__device__ __forceinline__ double fpow<double>(double b, double e) { return e == 2.0 ? b * b : pow(b, e); }
+
+struct RepParams {
+  int nx, ny, nz;
+  long long n;
+  int color_norm, psi_kind;
+  double inv_rho_r0, inv_rho_b0, grad_eps, pi, chi;
+};
+
+__device__ __forceinline__ long long wrap_index(int x, int y, int z, int nx, int ny, int nz) {
+  x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+  z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+  return x + (long long)nx * (y + (long long)ny * z);
+}
+
+// normals[3][N] (zero where undefined)
+template <class L, class T>
+__global__ void normals_kernel(const T* __restrict__ colour, const uint8_t* __restrict__ solid,
+                               T* __restrict__ normals, RepParams a) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(m % a.nx), y = (int)((m / a.nx) % a.ny), z = (int)(m / ((long long)a.nx * a.ny));
+    T g[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < L::NP; q++) {
+      const long long mp = wrap_index(x + L::pcx(q), y + L::pcy(q), z + L::pcz(q), a.nx, a.ny, a.nz);
+      const long long mm = wrap_index(x - L::pcx(q), y - L::pcy(q), z - L::pcz(q), a.nx, a.ny, a.nz);
+      const T vp = (solid && solid[mp]) ? colour[m] : colour[mp];
+      const T vm = (solid && solid[mm]) ? colour[m] : colour[mm];
+      const T d = T(3.0 * L::w(L::pgrp(q))) * (vp - vm);
+      if (L::pcx(q)) g[0] += L::pcx(q) * d;
+      if (L::pcy(q)) g[1] += L::pcy(q) * d;
+      if (L::pcz(q)) g[2] += L::pcz(q) * d;
+    }
+    const T gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const bool ok = gn > T(a.grad_eps) && !(solid && solid[m]);
+    for (int d = 0; d < 3; d++) normals[(long long)d * a.n + m] = ok ? g[d] / gn : T(0);
+  }
+}
+
+// F_rep at node (x, y, z) from the normal and colour fields (Eq. repForce).
+template <class L, class T>
+__device__ __forceinline__ void rep_force(const T* __restrict__ normals, const T* __restrict__ colour,
+                                          const uint8_t* __restrict__ solid, int x, int y, int z, const RepParams& a,
+                                          T (&F)[3]) {
+  F[0] = F[1] = F[2] = T(0);
+  const long long m = x + (long long)a.nx * (y + (long long)a.ny * z);
+  const T n0 = normals[m], n1 = normals[a.n + m], n2 = normals[2 * a.n + m];
+  if (n0 == T(0) && n1 == T(0) && n2 == T(0)) return;  // no normal at x
+  T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 1; i < L::Q; i++) {
+    const long long mm = wrap_index(x + cx<L>(i), y + cy<L>(i), z + cz<L>(i), a.nx, a.ny, a.nz);
+    if (solid && solid[mm]) continue;
+    const T p0 = normals[mm], p1 = normals[a.n + mm], p2 = normals[2 * a.n + mm];
+    const T nc = cx<L>(i) * n0 + cy<L>(i) * n1 + cz<L>(i) * n2;
+    const T pc = cx<L>(i) * p0 + cy<L>(i) * p1 + cz<L>(i) * p2;
+    if (-(nc * pc) > T(0)) {  // H(0) = 0; an undefined neighbour normal gives pc = 0
+      const T il = grp<L>(i) == 1 ? T(1) : T(0.70710678118654752440);
+      acc[0] += (nc * n0 + pc * p0) * il;
+      acc[1] += (nc * n1 + pc * p1) * il;
+      acc[2] += (nc * n2 + pc * p2) * il;
+    }
+  }
+  const T c = colour[m];
+  const T base = a.psi_kind ? T(1) + fabs(c) : T(1) - fabs(c);
+  const T s = T(a.pi) * fpow<T>(base, T(a.chi));
+  for (int d = 0; d < 3; d++) F[d] = s * acc[d];
+}
+
+}  // namespace lbm

@@ -37,6 +37,7 @@
 #include <cstdint>
 
 #include "lbm_lattice.cuh"
+#include "lbm_rep.cuh"
 
 namespace lbm {
 
@@ -176,7 +177,7 @@ __device__ __forceinline__ CompState<T> comp_state(const T* g, T r_old) {
 // the summed equilibrium sum_k f^{k,eq}, whose enhanced part involves grad(rho_R + rho_B).
 template <class L, class T, class NB>
 __device__ __forceinline__ void cg_collide(const StepParams<T>& p, T (&g)[2][L::Q], const CompState<T>& cr,
-                                           const CompState<T>& cb, const NB& nbr) {
+                                           const CompState<T>& cb, const NB& nbr, const T (&Fx)[3]) {
   constexpr int Q = L::Q;
   // gradients of the total density and of rho^N: grad phi = 3 sum_i w_i phi(x+c_i) c_i,
   // summed as opposite-pair differences
@@ -211,8 +212,9 @@ __device__ __forceinline__ void cg_collide(const StepParams<T>& p, T (&g)[2][L::
     if (L::pcy(q)) jm[1] += L::pcy(q) * dd;
     if (L::pcz(q)) jm[2] += L::pcz(q) * dd;
   }
-  T F[3] = {T(0), T(0), T(0)};
-  if (p.has_body) { F[0] = p.body[0]; F[1] = p.body[1]; F[2] = p.body[2]; }
+  // body force plus the extra (repulsion) force
+  T F[3] = {Fx[0], Fx[1], Fx[2]};
+  if (p.has_body) { F[0] += p.body[0]; F[1] += p.body[1]; F[2] += p.body[2]; }
   T u[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) u[a] = (jm[a] + T(0.5) * F[a]) * inv;
@@ -402,10 +404,13 @@ __host__ size_t step_smem_bytes(int tx, int ty) {
 template <class T>
 __host__ __device__ constexpr int min_blocks() { return sizeof(T) == 8 ? 1 : 2; }
 
-template <class L, class T, class S, class RT, int MODEL, bool WALLS>
+// REP (CG only): add the repulsion force of Eq. repForce from the pre-pass fields
+// colour / normals (lbm_rep.cuh).
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
     const S* __restrict__ fin, S* __restrict__ fout, const RT* __restrict__ rin, RT* __restrict__ rout,
-    const uint8_t* __restrict__ solid, const int* __restrict__ status, StepParams<T> p) {
+    const uint8_t* __restrict__ solid, const int* __restrict__ status, StepParams<T> p,
+    const T* __restrict__ colour, const T* __restrict__ normals, RepParams rp) {
   constexpr int Q = L::Q;
   constexpr int K = ModelTraits<MODEL>::K, NF = ModelTraits<MODEL>::NF;
   constexpr int NPL = planes_of<L>();
@@ -487,7 +492,9 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
       return fld[(sl * NV + fi) * NE + e];
     };
     if constexpr (MODEL == kCG) {
-      cg_collide<L, T>(p, g, cs[0], cs[1], nbr);
+      T Fx[3] = {T(0), T(0), T(0)};
+      if constexpr (REP) rep_force<L, T>(normals, colour, WALLS ? solid : nullptr, gx, gy, z, rp, Fx);
+      cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
     } else if constexpr (MODEL == kSCMP) {
       scmp_collide<L, T>(p, g, cs[0], nbr);
     } else {

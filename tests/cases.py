@@ -75,14 +75,51 @@ def sc_walls2d(nx=24, ny=20, **extra):
     return Case("sc_walls2d", kw, rho, None, None, solid)
 
 
+def cg_rep3d(nx=30, ny=16, nz=15, seed=6, **extra):
+    """Two droplets two nodes apart: the CG repulsion force (Eq. repForce) acts in the gap."""
+    x, y, z = inputs.grid(nx, ny, nz)
+    d1 = (x - 8.5) ** 2 + (y - 7.5) ** 2 + (z - 7) ** 2 <= 5.2 ** 2
+    d2 = (x - 20.5) ** 2 + (y - 7.5) ** 2 + (z - 7) ** 2 <= 5.2 ** 2
+    rr, rb = inputs.two_fluid(d1 | d2, 1.0, 1.0, 0.01, seed)
+    kw = dict(lattice=1, model=0, nx=nx, ny=ny, nz=nz, rho_r0=1.0, rho_b0=1.0, A=5e-3, rep_pi=0.02, rep_chi=2.0,
+              grad_eps=1e-7)
+    kw.update(extra)
+    return Case("cg_rep3d", kw, rr, rb)
+
+
+def cg_rep_film(nx=41, ny=6, nz=5, **extra):
+    """Two red slabs and a 4-node blue film, seeded noise.  At the film centre rho^N has an
+    extremum with both colours present, so grad_eps = 1e-4 switches off the recolouring
+    direction where |grad rho^N| is below FP32 resolution."""
+    x, _, _ = inputs.grid(nx, ny, nz)
+    film = (x >= 19) & (x < 23)
+    red = ~film & (np.abs(x - 20.5) < 14)
+    rr, rb = inputs.two_fluid(red, 1.0, 1.0, 0.01, 8)
+    kw = dict(lattice=1, model=0, nx=nx, ny=ny, nz=nz, rho_r0=1.0, rho_b0=1.0, A=5e-3, rep_pi=0.01, rep_chi=2.0,
+              grad_eps=1e-4, rep_psi_kind=0)
+    kw.update(extra)
+    return Case("cg_rep_film", kw, rr, rb)
+
+
 SMALL_CASES = {
     "cg_drop3d": cg_drop3d,
+    # sizes the TMA-staged kernel takes (nx % 32 == 0, ny % 8 == 0)
+    "cg_tma3d": lambda: cg_drop3d(nx=32, ny=16, nz=13),
+    "cg_tma_walls": lambda: cg_walls3d(nx=32, ny=16, nz=9),
+    "sc_tma3d": lambda: sc_mp3d(nx=32, ny=16, nz=14),
+    "sc2c_tma3d": lambda: sc_2c3d(nx=64, ny=24, nz=5),
     "cg_drop2d": cg_drop2d,
     "cg_walls3d": cg_walls3d,
     "cg_std_norm": lambda: cg_drop3d(enhanced_eq=0, color_norm=1, ratio=4.0),
     "sc_mp3d": sc_mp3d,
     "sc_2c3d": sc_2c3d,
     "sc_walls2d": sc_walls2d,
+    "cg_rep3d": cg_rep3d,
+    "cg_rep_film": cg_rep_film,
+    # the printed psi_rep = (1 + |rho^N|)^chi is largest where |grad rho^N| is near zero and
+    # the normal is rounding noise (Pi = 0.02 blows up within 90 steps on the oracle); a
+    # grad_eps of 1e-3 keeps only well-defined normals
+    "cg_rep_walls": lambda: cg_walls3d(rep_pi=0.001, rep_chi=1.5, grad_eps=1e-3, rep_psi_kind=1),
 }
 
 
