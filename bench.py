@@ -182,6 +182,19 @@ def run_ours(args):
     sc = lbm.Lattice(lbm.Params(precision=lbm.FP32, **sc_kw()))
     cg.init(t(rr), t(rb))
     sc.init(t(rho))
+    from paper_2110_05197_gb300 import tune
+    tiling = {}
+    if args.tiling:
+        tx, ty, tz = (int(v) for v in args.tiling.split(","))
+        cg.set_tiling(tx, ty, tz)
+        sc.set_tiling(tx, ty, tz)
+        tiling = {"cg": [tx, ty, tz], "sc": [tx, ty, tz], "tuned": False}
+    else:
+        best_cg, tm_cg = tune.autotune(cg)
+        best_sc, tm_sc = tune.autotune(sc)
+        tiling = {"cg": list(best_cg), "sc": list(best_sc), "tuned": True,
+                  "cg_ms": {"x".join(map(str, k)): round(v, 4) for k, v in tm_cg.items()},
+                  "sc_ms": {"x".join(map(str, k)): round(v, 4) for k, v in tm_sc.items()}}
     if args.profile_only:
         lat = cg if args.profile_only == "cg" else sc
         lat.step(args.warmup + args.steps)
@@ -268,6 +281,7 @@ def run_ours(args):
             "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                     "request": f"init from pinned host fields + {K} CG and {K} SC steps + densities/totals to host"},
             "gpu_launches": launches,
+            "tiling": tiling,
             "status": {"cg": lbm.status_string(rc_cg), "sc": lbm.status_string(rc_sc),
                        "cg_mass_r": tot_cg["mass_r"], "sc_mass": tot_sc["mass_r"]},
         }
@@ -289,6 +303,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiling", default=None, help="tx,ty,tz for both lattices (default: autotuned)")
     ap.add_argument("--profile-only", default=None, choices=["cg", "sc"],
                     help="profiling runs: warm up and step only this lattice, print nothing")
     args = ap.parse_args()

@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm_lattice.cuh"
 #include "lbm_rep.cuh"
@@ -99,6 +100,9 @@ __device__ __forceinline__ float fexp(float x) { return expf(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
+// correctly rounded reciprocal (cheaper than a full division in FP32)
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 
 __host__ __device__ __forceinline__ int wrap(int v, int n) {
   int r = v % n;
@@ -123,9 +127,9 @@ __device__ __forceinline__ void node_fields(const StepParams<T>& p, T s0, T s1, 
     out[0] = rho;
     if (p.color_norm) {
       T a = s0 * p.inv_rho_r0, b = s1 * p.inv_rho_b0;
-      out[1] = (a - b) / (a + b);
+      out[1] = (a - b) * frcp(a + b);
     } else {
-      out[1] = (s0 - s1) / rho;
+      out[1] = (s0 - s1) * frcp(rho);
     }
   } else if constexpr (MODEL == kSCMP) {
     out[0] = p.rho0 * (T(1) - fexp(-s0 * p.inv_rho0));  // Eq. pseudopotential
@@ -194,7 +198,7 @@ __device__ __forceinline__ void cg_collide(const StepParams<T>& p, T (&g)[2][L::
   }
   const T rr = cr.rho, rb = cb.rho;
   const T rho = rr + rb;
-  const T inv = T(1) / rho;
+  const T inv = frcp(rho);
   // total deviation relative to s_i = phi^R_i q_R + phi^B_i q_B
   T G[Q];
 #pragma unroll
@@ -215,12 +219,13 @@ __device__ __forceinline__ void cg_collide(const StepParams<T>& p, T (&g)[2][L::
   // body force plus the extra (repulsion) force
   T F[3] = {Fx[0], Fx[1], Fx[2]};
   if (p.has_body) { F[0] += p.body[0]; F[1] += p.body[1]; F[2] += p.body[2]; }
+  const bool forced = F[0] != T(0) || F[1] != T(0) || F[2] != T(0);
   T u[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) u[a] = (jm[a] + T(0.5) * F[a]) * inv;
-  // Eq. interpVisc and Eq. effRelax
-  const T nubar = T(1) / ((rr * p.inv_nu_r + rb * p.inv_nu_b) * inv);
-  const T omega = T(2) / (T(6) * nubar + T(1));
+  // Eq. interpVisc and Eq. effRelax: 1/nubar = (rho_R/nu_R + rho_B/nu_B)/rho
+  const T nubar = rho * frcp(rr * p.inv_nu_r + rb * p.inv_nu_b);
+  const T omega = T(2) * frcp(T(6) * nubar + T(1));
   const T en = p.enhanced ? nubar : T(0);
   const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T ugr = u[0] * gr[0] + u[1] * gr[1] + u[2] * gr[2];
@@ -230,58 +235,79 @@ __device__ __forceinline__ void cg_collide(const StepParams<T>& p, T (&g)[2][L::
   const T gabs = fsqrt(gg);
   const bool hasg = gabs > p.grad_eps;
   const T Ag = hasg ? p.A * gabs : T(0);
-  const T inv_gg = hasg ? T(1) / gg : T(0);
-  const T inv_g = hasg ? T(1) / gabs : T(0);
+  const T inv_g = hasg ? frcp(gabs) : T(0);
+  const T inv_gg = inv_g * inv_g;
   const T cR = rr * inv;
   const T rec = p.beta * rr * rb * inv * inv;
   // Equilibrium relative to s: f^eq_i - s_i = sum_k phi^k_i (rho_k - q_k) + velocity and
   // enhanced parts, with rho_k - q_k = dq_k exact (a few ulps of the density)
   const T dR = cr.dq, dB = cb.dq;
+  // per-group constants (group 1: axis, 2: diagonal)
+  T c_rest[3], c_u2[3], c_uu[3], c_od[3], c_fe[3], c_rc[3], c_base[3], c_sev[3], c_sod[3];  // [0] unused
+#pragma unroll
+  for (int gi = 1; gi <= 2; gi++) {
+    const T w = T(L::w(gi));
+    const T phR = p.phi[0][gi], phB = p.phi[1][gi];
+    c_rest[gi] = en * T(L::psi(gi)) * ugr + phR * dR + phB * dB - rho * w * T(1.5) * uu;  // even, u-independent of c
+    c_u2[gi] = rho * w * T(4.5);
+    c_uu[gi] = en * T(2.0 * L::xi(gi));
+    c_od[gi] = rho * w * T(3);
+    c_fe[gi] = rr * phR + rb * phB;                                        // f^eq|_{u=0}
+    c_rc[gi] = rec * c_fe[gi] * inv_g * ((gi == 1) ? T(1) : T(0.70710678118654752440));
+    c_base[gi] = (rr * phB * cb.q - rb * phR * cr.q) * inv;
+    c_sev[gi] = w * kg;
+    c_sod[gi] = w * kg * T(3);
+  }
   // rest direction (cos phi_0 = 0, c_0 = 0)
   {
     const T eq = en * T(L::psi(0)) * ugr + rho * T(L::w(0)) * (T(-1.5) * uu) + p.phi[0][0] * dR + p.phi[1][0] * dB;
     T Gs = G[0] + omega * (eq - G[0]);
-    Gs += T(L::w(0)) * kg * (T(-3) * uF);
+    if (forced) Gs += T(L::w(0)) * kg * (T(-3) * uF);
     Gs -= Ag * T(L::B(0));
     const T base = (rr * p.phi[1][0] * cb.q - rb * p.phi[0][0] * cr.q) * inv;
     const T gR = cR * Gs + base;
     g[0][0] = gR;
     g[1][0] = Gs - gR;
   }
+  auto pairs = [&](auto with_force) {
+    constexpr bool FORCE = decltype(with_force)::value;
 #pragma unroll
-  for (int q = 0; q < L::NP; q++) {
-    const int i = 2 * q + 1, j = 2 * q + 2;
-    const int gi = L::pgrp(q);
-    const T w = T(L::w(gi));
-    const T cu = T(L::pcx(q)) * u[0] + T(L::pcy(q)) * u[1] + T(L::pcz(q)) * u[2];
-    const T cg = T(L::pcx(q)) * gr[0] + T(L::pcy(q)) * gr[1] + T(L::pcz(q)) * gr[2];
-    const T cn = T(L::pcx(q)) * gn[0] + T(L::pcy(q)) * gn[1] + T(L::pcz(q)) * gn[2];
-    const T cF = T(L::pcx(q)) * F[0] + T(L::pcy(q)) * F[1] + T(L::pcz(q)) * F[2];
-    const T phR = p.phi[0][gi], phB = p.phi[1][gi];
-    // Eq. equiliCG summed over colours, minus phi^k q_k: even and odd parts in c_i
-    const T ev = en * (T(L::psi(gi)) * ugr + T(2.0 * L::xi(gi)) * cu * cg) + phR * dR + phB * dB +
-                 rho * w * (T(4.5) * cu * cu - T(1.5) * uu);
-    const T od = rho * w * T(3) * cu;
-    // Eq. source (Guo) with tau = 1/omega_eff
-    const T sev = w * kg * (T(9) * cu * cF - T(3) * uF);
-    const T sod = w * kg * T(3) * cF;
-    // Eq. perturbationOp (A|grad rho^N| on the total), even in c_i
-    const T pert = hasg ? Ag * (w * cn * cn * inv_gg - T(L::B(gi))) : T(0);
-    const T Gsi = G[i] + omega * (ev + od - G[i]) + sev + sod + pert;
-    const T Gsj = G[j] + omega * (ev - od - G[j]) + sev - sod + pert;
-    // Eqs. recoloringOpR/B with cos(phi_i) = c_i.grad rho^N / (|c_i| |grad rho^N|) and
-    // f^eq|_{u=0} = sum_k rho_k phi^k_i; red part relative to phi^R q_R
-    const T feq0 = rr * phR + rb * phB;
-    const T inv_len = (gi == 1) ? T(1) : T(0.70710678118654752440);
-    const T rc = rec * (cn * inv_g * inv_len) * feq0;
-    const T base = (rr * phB * cb.q - rb * phR * cr.q) * inv;
-    const T gRi = cR * Gsi + base + rc;
-    const T gRj = cR * Gsj + base - rc;
-    g[0][i] = gRi;
-    g[1][i] = Gsi - gRi;
-    g[0][j] = gRj;
-    g[1][j] = Gsj - gRj;
-  }
+    for (int q = 0; q < L::NP; q++) {
+      const int i = 2 * q + 1, j = 2 * q + 2;
+      const int gi = L::pgrp(q);
+      const T cu = T(L::pcx(q)) * u[0] + T(L::pcy(q)) * u[1] + T(L::pcz(q)) * u[2];
+      const T cg = T(L::pcx(q)) * gr[0] + T(L::pcy(q)) * gr[1] + T(L::pcz(q)) * gr[2];
+      const T cn = T(L::pcx(q)) * gn[0] + T(L::pcy(q)) * gn[1] + T(L::pcz(q)) * gn[2];
+      // Eq. equiliCG summed over colours, minus phi^k q_k: even and odd parts in c_i
+      const T ev = c_rest[gi] + cu * (c_u2[gi] * cu + c_uu[gi] * cg);
+      const T od = c_od[gi] * cu;
+      // Eq. perturbationOp (A|grad rho^N| on the total), even in c_i
+      const T pert = Ag * (T(L::w(gi)) * cn * cn * inv_gg - T(L::B(gi)));
+      T Gsi = G[i] + omega * (ev + od - G[i]) + pert;
+      T Gsj = G[j] + omega * (ev - od - G[j]) + pert;
+      if constexpr (FORCE) {
+        // Eq. source (Guo) with tau = 1/omega_eff: even and odd parts
+        const T cF = T(L::pcx(q)) * F[0] + T(L::pcy(q)) * F[1] + T(L::pcz(q)) * F[2];
+        const T sev = c_sev[gi] * (T(9) * cu * cF - T(3) * uF);
+        const T sod = c_sod[gi] * cF;
+        Gsi += sev + sod;
+        Gsj += sev - sod;
+      }
+      // Eqs. recoloringOpR/B with cos(phi_i) = c_i.grad rho^N / (|c_i| |grad rho^N|) and
+      // f^eq|_{u=0} = sum_k rho_k phi^k_i; red part relative to phi^R q_R
+      const T rc = c_rc[gi] * cn;
+      const T gRi = cR * Gsi + c_base[gi] + rc;
+      const T gRj = cR * Gsj + c_base[gi] - rc;
+      g[0][i] = gRi;
+      g[1][i] = Gsi - gRi;
+      g[0][j] = gRj;
+      g[1][j] = Gsj - gRj;
+    }
+  };
+  if (forced)
+    pairs(std::true_type{});
+  else
+    pairs(std::false_type{});
 }
 
 // ---------------------------------------------------------------------------------------
@@ -352,7 +378,7 @@ __device__ __forceinline__ void scmp_collide(const StepParams<T>& p, T (&g)[1][L
   for (int a = 0; a < 3; a++) F[a] = -p.G * psic * acc[a] + (p.has_body ? p.body[a] : T(0));
   T jm[3];
   momentum<L, T>(g[0], jm);
-  const T inv = T(1) / c.rho;
+  const T inv = frcp(c.rho);
   T u[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) u[a] = (jm[a] + T(0.5) * F[a]) * inv;
@@ -364,7 +390,7 @@ __device__ __forceinline__ void sc2c_collide(const StepParams<T>& p, T (&g)[2][L
                                              const CompState<T>& c2, const NB& nbr) {
   const T r1 = c1.rho, r2 = c2.rho;
   const T rho = r1 + r2;
-  const T inv = T(1) / rho;
+  const T inv = frcp(rho);
   T a1[3], a2[3];
   weighted_sum<L, T>(nbr, 1, a1);  // sum w_i rho_2(x+c_i) c_i
   weighted_sum<L, T>(nbr, 0, a2);  // sum w_i rho_1(x+c_i) c_i

@@ -216,6 +216,8 @@ class Lattice:
         """Arrays may be torch tensors (device or host) or numpy arrays, FP64 (uint8 for
         solid), contiguous, node-ordered."""
         self._keep = (rho_r, rho_b, u, solid, pops)
+        self._solid = solid
+        self._has_walls = solid is not None
         _check(lib().lbm_init_fields(self._h, _ptr(rho_r), _ptr(rho_b), _ptr(u), _ptr(solid), _ptr(pops)),
                "lbm_init_fields")
         return self
@@ -281,5 +283,7 @@ class Lattice:
 
     def load_state(self, state, solid=None):
         self._keep_state = (state, solid)
+        self._solid = solid
+        self._has_walls = solid is not None
         _check(lib().lbm_load_state(self._h, _ptr(state), _ptr(solid)), "lbm_load_state")
         return self

@@ -1,0 +1,71 @@
+"""Launch-shape autotuner for the fused step kernel.
+
+For a lattice it times a handful of tilings (block columns tx x ty, z planes per block tz;
+32 x 8 selects the TMA-staged kernel where the lattice allows it) on the lattice's own
+state, keeps the fastest, and restores the state bit for bit (raw state save/load), so
+tuning never changes a simulation's result.  The choice is cached per lattice shape,
+model, precision, walls and repulsion so that every lattice of a shape runs the same
+kernel (results then do not depend on what else was tuned or batched).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import lbm
+
+CANDIDATES_3D = [(32, 8, 16), (32, 8, 32), (32, 4, 16), (32, 4, 32), (64, 4, 16), (64, 4, 32),
+                 (64, 2, 32), (128, 2, 16), (32, 2, 32), (16, 8, 16)]
+CANDIDATES_2D = [(32, 8, 1), (32, 4, 1), (64, 4, 1), (128, 2, 1), (256, 1, 1), (64, 2, 1)]
+
+_cache: dict = {}
+
+
+def shape_key(lat: "lbm.Lattice"):
+    p = lat.params
+    return (p.lattice, p.model, p.precision, p.nx, p.ny, p.nz, getattr(lat, "_has_walls", False),
+            p.model == lbm.CG and p.rep_pi != 0.0)
+
+
+def candidates_for(p: "lbm.Params"):
+    cands = CANDIDATES_3D if p.lattice == lbm.D3Q19 else CANDIDATES_2D
+    out = []
+    for tx, ty, tz in cands:
+        tz = min(tz, p.nz)
+        if (tx, ty, tz) not in out:
+            out.append((tx, ty, tz))
+    return out
+
+
+def time_steps(lat: "lbm.Lattice", steps: int) -> float:
+    s = lat.stream
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    lat.step(steps)
+    b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def autotune(lat: "lbm.Lattice", candidates=None, steps: int = 3, use_cache: bool = True):
+    """Pick the fastest tiling for `lat` (state restored afterwards).  Returns
+    (best tiling, {tiling: ms per step})."""
+    key = shape_key(lat)
+    if use_cache and key in _cache:
+        lat.set_tiling(*_cache[key][0])
+        return _cache[key]
+    state = lat.save_state()
+    solid = getattr(lat, "_solid", None)
+    timings = {}
+    for t in (candidates or candidates_for(lat.params)):
+        try:
+            lat.set_tiling(*t)
+        except lbm.LbmError:
+            continue
+        lat.load_state(state, solid)
+        lat.step(1)  # warm (first launch of a variant sets its shared-memory attribute)
+        timings[t] = time_steps(lat, steps)
+    best = min(timings, key=timings.get)
+    lat.set_tiling(*best)
+    lat.load_state(state, solid)
+    _cache[key] = (best, timings)
+    return best, timings

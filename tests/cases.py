@@ -76,10 +76,12 @@ def sc_walls2d(nx=24, ny=20, **extra):
 
 
 def cg_rep3d(nx=30, ny=16, nz=15, seed=6, **extra):
-    """Two droplets two nodes apart: the CG repulsion force (Eq. repForce) acts in the gap."""
+    """Two droplets about two nodes apart, with different radii and offset centres so that
+    the normals in the gap are generic (no symmetry puts a Heaviside argument at FP32
+    resolution): the CG repulsion force (Eq. repForce) acts in the gap."""
     x, y, z = inputs.grid(nx, ny, nz)
     d1 = (x - 8.5) ** 2 + (y - 7.5) ** 2 + (z - 7) ** 2 <= 5.2 ** 2
-    d2 = (x - 20.5) ** 2 + (y - 7.5) ** 2 + (z - 7) ** 2 <= 5.2 ** 2
+    d2 = (x - 19.7) ** 2 + (y - 8.8) ** 2 + (z - 7.9) ** 2 <= 4.6 ** 2
     rr, rb = inputs.two_fluid(d1 | d2, 1.0, 1.0, 0.01, seed)
     kw = dict(lattice=1, model=0, nx=nx, ny=ny, nz=nz, rho_r0=1.0, rho_b0=1.0, A=5e-3, rep_pi=0.02, rep_chi=2.0,
               grad_eps=1e-7)
