@@ -71,7 +71,7 @@ cudaError_t launch_tma_t(lbm_ctx* c) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 block(TX, TY, 1);
+  dim3 block(kTmaThreads, 1, 1);
   dim3 grid(c->p.nx / TX, c->p.ny / TY, (c->p.nz + c->tz - 1) / c->tz);
   const StepParams<T> sp = make_step_params<T>(c);
   S* fout = static_cast<S*>(c->f[c->cur ^ 1]);

@@ -124,84 +124,87 @@ struct TmaLayout {
 
 constexpr int kStatusLayout = 0x200;  // diag status bit: shared-memory base not 128-byte aligned
 
-// Shared memory: [0, 128) the three mbarriers; then three plane buffers (128-byte
-// aligned); then the rotating stencil-field planes; then the wall masks.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_addr(bar)) : "memory");
+  (void)state;
+}
+
+// Warp roles of the TMA-staged kernel.
+constexpr int kCollideWarps = 8;  // one node per thread of the TX x TY = 32 x 8 tile
+constexpr int kStageWarps = 4;    // reduce each staged plane to its stencil fields
+constexpr int kTmaThreads = 32 * (kCollideWarps + kStageWarps + 1);  // + one producer warp
+constexpr int kRawSlots = 3, kFieldSlots = 4;
+
+// Shared memory: [0, 128) the mbarriers; then the raw plane buffers (128-byte aligned);
+// then the stencil-field slots; then the wall-mask slots.
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
 __host__ __device__ constexpr size_t tma_smem_bytes() {
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
-  return 128 + 3 * Lay::BUF + 3 * NV * Lay::NE * sizeof(T) + (WALLS ? 3 * Lay::NE : 0);
+  return 128 + kRawSlots * Lay::BUF + kFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kFieldSlots * Lay::NE : 0);
 }
 
+// Pipeline over the planes j = 0 .. n-1 of a block's z-chunk (plane z = z0 - 1 + j; j = 0
+// and j = n-1 are the halo planes):
+//   producer : raw_full[j%3] <- tensor copies of plane j, after raw_free[j%3] reports
+//              plane j-3 finished (staging and collision);
+//   staging  : waits raw_full, and fld_free[j%4] for plane j-4's fields; writes the fields of
+//              plane j into slot j%4; arrives fld_full[j%4] and raw_free[j%3];
+//   collision: for planes c = 1 .. n-2 waits fld_full of c+1 (c-1, c were waited earlier)
+//              and raw_full of c; collides and pushes; arrives raw_free[c%3] and
+//              fld_free[(c-1)%4] (the last use of plane c-1's fields).
+// No block-wide barrier inside the loop; every wait is bounded and a timeout sets the
+// status word, so no thread can hang.
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 1)
+__global__ void __launch_bounds__(kTmaThreads, 1)
     step_kernel_tma(const __grid_constant__ TmaMaps maps, S* __restrict__ fout, RT* __restrict__ rout,
                     const uint8_t* __restrict__ solid, int* __restrict__ status, StepParams<T> p) {
+  static_assert(TX * TY == 32 * kCollideWarps, "one collision thread per tile node");
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int Q = L::Q, K = Lay::K, KQ = Lay::KQ, SW = Lay::SW, RSW = Lay::RSW;
   constexpr int NF = ModelTraits<MODEL>::NF, NV = NF + K;
-  constexpr int EX = Lay::EX, NE = Lay::NE, NI = Lay::NI;
+  constexpr int EX = Lay::EX, NE = Lay::NE;
   if (*status != 0) return;  // blown-up (or timed-out) state: stop stepping
 
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);           // [3]
-  unsigned char* bufs = smem + 128;                              // [3][BUF]
-  T* fld = reinterpret_cast<T*>(bufs + 3 * Lay::BUF);           // [3][NV][NE]
-  uint8_t* msk = reinterpret_cast<uint8_t*>(fld + 3 * NV * NE);  // [3][NE]
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);  // [3]
+  uint64_t* raw_free = raw_full + kRawSlots;                // [3]
+  uint64_t* fld_full = raw_free + kRawSlots;                // [4]
+  uint64_t* fld_free = fld_full + kFieldSlots;              // [4]
+  unsigned char* bufs = smem + 128;                         // [3][BUF]
+  T* fld = reinterpret_cast<T*>(bufs + kRawSlots * Lay::BUF);      // [4][NV][NE]
+  uint8_t* msk = reinterpret_cast<uint8_t*>(fld + kFieldSlots * NV * NE);  // [4][NE]
 
-  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * p.tz;
   const int z1 = min(z0 + p.tz, p.nz);
+  const int np = z1 - z0 + 2;  // planes z0-1 .. z1
   const long long N = p.n;
 
-  // the plane buffers start 128 bytes into dynamic shared memory; refuse to issue any copy
-  // if the base is not 128-byte aligned (uniform over the block)
-  if (smem_addr(bufs) & 127u) {
+  if (smem_addr(bufs) & 127u) {  // copy destinations must be 128-byte aligned
     if (tid == 0) atomicOr(status, kStatusLayout);
     return;
   }
   if (tid == 0) {
-    for (int b = 0; b < 3; b++) mbar_init(&bars[b], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.pop_main_mid) : "memory");
-  }
-  __syncthreads();
-
-  // plane p -> ring slot (buffers and field planes rotate together)
-  auto slot = [&](int pl) { return (pl - z0 + 1) % 3; };
-  const int yt = y0 == 0 ? p.ny - 1 : y0 - 1, yb = y0 + TY == p.ny ? 0 : y0 + TY;
-  const int xl = x0 == 0 ? p.nx - SW : x0 - SW, xr = x0 + TX == p.nx ? 0 : x0 + TX;
-  const int xlr = x0 == 0 ? p.nx - RSW : x0 - RSW, xrr = x0 + TX == p.nx ? 0 : x0 + TX;
-  bool pending[3] = {false, false, false};  // thread 0: copies issued, not yet waited for
-  auto issue = [&](int pl) {  // thread 0 only
-    const int gz = wrap(pl, p.nz);
-    const int s = slot(pl);
-    pending[s] = true;
-    unsigned char* b = bufs + s * Lay::BUF;
-    uint64_t* bar = &bars[s];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(bar, Lay::TX_BYTES);
-    const int rows_y[3] = {yt, y0, yb};
-    for (int g = 0; g < 3; g++) {
-      const bool mid = g == 1;
-      const int y = rows_y[g];
-      tma_load_4d(b + Lay::PM::group(g), mid ? &maps.pop_main_mid : &maps.pop_main_row, x0, 0, y, gz, bar);
-      tma_load_4d(b + Lay::OFF_L + Lay::PS::group(g), mid ? &maps.pop_strip_mid : &maps.pop_strip_row, xl, 0, y, gz,
-                  bar);
-      tma_load_4d(b + Lay::OFF_R + Lay::PS::group(g), mid ? &maps.pop_strip_mid : &maps.pop_strip_row, xr, 0, y, gz,
-                  bar);
-      tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), mid ? &maps.ref_main_mid : &maps.ref_main_row, x0, 0, y, gz,
-                  bar);
-      tma_load_4d(b + Lay::OFF_RL + Lay::RSR::group(g), mid ? &maps.ref_strip_mid : &maps.ref_strip_row, xlr, 0, y,
-                  gz, bar);
-      tma_load_4d(b + Lay::OFF_RR + Lay::RSR::group(g), mid ? &maps.ref_strip_mid : &maps.ref_strip_row, xrr, 0, y,
-                  gz, bar);
+    for (int s = 0; s < kRawSlots; s++) {
+      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_free[s], kCollideWarps + kStageWarps);
     }
-  };
+    for (int s = 0; s < kFieldSlots; s++) {
+      mbar_init(&fld_full[s], kStageWarps);
+      mbar_init(&fld_free[s], kCollideWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // the only block-wide barrier: barriers initialised
 
-  // Ext-node views into a plane buffer: (base, stride) such that array a of the node is
-  // base[a * stride]; populations and reference densities.
+  auto plane_z = [&](int j) { return wrap(z0 - 1 + j, p.nz); };
+  auto give_up = [&]() { atomicOr(status, kStatusTimeout); };
+
+  // Ext-node views into a plane buffer: base pointers and strides of the node's arrays.
   struct View {
     const S* pop;
     int ps;
@@ -229,171 +232,177 @@ __global__ void __launch_bounds__(TX* TY, 1)
     return v;
   };
 
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  // ring task of this thread (84 ring nodes for 32 x 8, spread three threads apart)
-  constexpr int NRING = 2 * EX + 2 * TY;
-  constexpr int RSTRIDE = NI / NRING > 0 ? NI / NRING : 1;
-  const bool has_ring = (tid % RSTRIDE == 0) && (tid / RSTRIDE < NRING);
-  int rex = 0, rey = 0;
-  if (has_ring) {
-    const int r = tid / RSTRIDE;
-    if (r < EX) {
-      rex = r;
-      rey = 0;
-    } else if (r < 2 * EX) {
-      rex = r - EX;
-      rey = TY + 1;
-    } else if (r < 2 * EX + TY) {
-      rex = 0;
-      rey = 1 + (r - 2 * EX);
-    } else {
-      rex = TX + 1;
-      rey = 1 + (r - 2 * EX - TY);
+  if (warp == kCollideWarps + kStageWarps) {
+    // ---------------- producer ----------------
+    if (lane != 0) return;
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.pop_main_mid) : "memory");
+    const int yt = y0 == 0 ? p.ny - 1 : y0 - 1, yb = y0 + TY == p.ny ? 0 : y0 + TY;
+    const int xl = x0 == 0 ? p.nx - SW : x0 - SW, xr = x0 + TX == p.nx ? 0 : x0 + TX;
+    const int xlr = x0 == 0 ? p.nx - RSW : x0 - RSW, xrr = x0 + TX == p.nx ? 0 : x0 + TX;
+    int issued = 0;
+    for (int j = 0; j < np; j++) {
+      const int s = j % kRawSlots;
+      if (j >= kRawSlots && !mbar_wait_bounded(&raw_free[s], ((j / kRawSlots) - 1) & 1)) {
+        give_up();
+        break;
+      }
+      const int gz = plane_z(j);
+      unsigned char* b = bufs + s * Lay::BUF;
+      uint64_t* bar = &raw_full[s];
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(bar, Lay::TX_BYTES);
+#pragma unroll
+      for (int g = 0; g < 3; g++) {
+        const bool mid = g == 1;
+        const int y = g == 0 ? yt : (g == 1 ? y0 : yb);
+        tma_load_4d(b + Lay::PM::group(g), mid ? &maps.pop_main_mid : &maps.pop_main_row, x0, 0, y, gz, bar);
+        tma_load_4d(b + Lay::OFF_L + Lay::PS::group(g), mid ? &maps.pop_strip_mid : &maps.pop_strip_row, xl, 0, y,
+                    gz, bar);
+        tma_load_4d(b + Lay::OFF_R + Lay::PS::group(g), mid ? &maps.pop_strip_mid : &maps.pop_strip_row, xr, 0, y,
+                    gz, bar);
+        tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), mid ? &maps.ref_main_mid : &maps.ref_main_row, x0, 0, y,
+                    gz, bar);
+        tma_load_4d(b + Lay::OFF_RL + Lay::RSR::group(g), mid ? &maps.ref_strip_mid : &maps.ref_strip_row, xlr, 0,
+                    y, gz, bar);
+        tma_load_4d(b + Lay::OFF_RR + Lay::RSR::group(g), mid ? &maps.ref_strip_mid : &maps.ref_strip_row, xrr, 0,
+                    y, gz, bar);
+      }
+      issued = j + 1;
     }
+    // wait (bounded) until the copies this block issued have landed before exiting
+    for (int j = issued - kRawSlots; j < issued; j++)
+      if (j >= 0) mbar_wait_bounded(&raw_full[j % kRawSlots], (j / kRawSlots) & 1);
+    return;
   }
-  const int rgx = wrap(x0 - 1 + rex, p.nx), rgy = wrap(y0 - 1 + rey, p.ny);
 
-  // densities and stencil fields of one ext node from a plane buffer
-  auto stage_node = [&](const unsigned char* b, int ex, int ey, int sl, int gxn, int gyn, int gz) {
-    const View v = view(b, ex, ey);
-    const int e = ey * EX + ex;
-    T rho[2] = {T(0), T(0)};
+  if (warp >= kCollideWarps) {
+    // ---------------- staging ----------------
+    const int stid = tid - 32 * kCollideWarps;
+    for (int j = 0; j < np; j++) {
+      const int s = j % kRawSlots, fs = j % kFieldSlots;
+      bool ok = mbar_wait_bounded(&raw_full[s], (j / kRawSlots) & 1);
+      if (ok && j >= kFieldSlots) ok = mbar_wait_bounded(&fld_free[fs], ((j / kFieldSlots) - 1) & 1);
+      if (!ok) {
+        give_up();
+        return;
+      }
+      const unsigned char* b = bufs + s * Lay::BUF;
+      const int gz = plane_z(j);
+      for (int e = stid; e < NE; e += 32 * kStageWarps) {
+        const int ey = e / EX, ex = e - ey * EX;
+        const View v = view(b, ex, ey);
+        T rho[2] = {T(0), T(0)};
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      T g[Q];
+        for (int k = 0; k < K; k++) {
+          T g[Q];
 #pragma unroll
-      for (int i = 0; i < Q; i++) g[i] = ld_s<S, T>(v.pop[(k * Q + i) * v.ps]);
-      const CompState<T> c = comp_state<L, T, RT>(g, T(v.ref[k * v.rs]));
-      rho[k] = c.rho;
-      fld[(sl * NV + NF + k) * NE + e] = c.q;
+          for (int i = 0; i < Q; i++) g[i] = ld_s<S, T>(v.pop[(k * Q + i) * v.ps]);
+          const CompState<T> c = comp_state<L, T, RT>(g, T(v.ref[k * v.rs]));
+          rho[k] = c.rho;
+          fld[(fs * NV + NF + k) * NE + e] = c.q;
+        }
+        T out[2];
+        node_fields<MODEL, T>(p, rho[0], rho[1], out);
+#pragma unroll
+        for (int f = 0; f < NF; f++) fld[(fs * NV + f) * NE + e] = out[f];
+        if (WALLS) {
+          const int gxn = wrap(x0 - 1 + ex, p.nx), gyn = wrap(y0 - 1 + ey, p.ny);
+          msk[fs * NE + e] = solid[gxn + (long long)p.nx * (gyn + (long long)p.ny * gz)];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&fld_full[fs]);
+        mbar_arrive(&raw_free[s]);
+      }
     }
-    T out[2];
-    node_fields<MODEL, T>(p, rho[0], rho[1], out);
-#pragma unroll
-    for (int f = 0; f < NF; f++) fld[(sl * NV + f) * NE + e] = out[f];
-    if (WALLS) msk[sl * NE + e] = solid[gxn + (long long)p.nx * (gyn + (long long)p.ny * gz)];
-  };
+    return;
+  }
 
+  // ---------------- collision ----------------
+  const int tx = tid % TX, ty = tid / TX;
   const int gx = x0 + tx, gy = y0 + ty;
-  auto stage_plane = [&](int pl) {
-    const int s = slot(pl);
-    const unsigned char* b = bufs + s * Lay::BUF;
-    const int gz = wrap(pl, p.nz);
-    stage_node(b, tx + 1, ty + 1, s, gx, gy, gz);
-    if (has_ring) stage_node(b, rex, rey, s, rgx, rgy, gz);
-  };
-
-  uint32_t phase[3] = {0, 0, 0};
-  auto wait_plane = [&](int pl) -> bool {
-    const int s = slot(pl);
-    const bool ok = mbar_wait_bounded(&bars[s], phase[s]);
-    phase[s] ^= 1;
-    pending[s] = false;
-    return ok;
-  };
-  // a wait gave up: flag it, and let thread 0 wait (bounded again) for the copies still
-  // in flight into this block's shared memory before the block exits
-  auto give_up = [&]() {
-    if (tid == 0) {
-      atomicOr(status, kStatusTimeout);
-      for (int s = 0; s < 3; s++)
-        if (pending[s]) mbar_wait_bounded(&bars[s], phase[s]);
-    }
-  };
-
   const int e0 = (ty + 1) * EX + (tx + 1);
   const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;
   const int ym = gy == 0 ? p.ny - 1 : gy - 1, yp = gy + 1 >= p.ny ? 0 : gy + 1;
   const long long nxl = p.nx;
   const long long plane_n = (long long)p.nx * p.ny;
   const long long rowm = ym * nxl, row0 = gy * nxl, rowp = yp * nxl;
+  if (lane == 0) mbar_arrive(&raw_free[0]);  // plane 0 is a halo plane: nothing to collide
 
-  auto collide = [&](int z) {
-    const int slm = slot(z - 1), sl0 = slot(z), slp = slot(z + 1);
-    if (WALLS && msk[sl0 * NE + e0]) return;
-    const View v = view(bufs + sl0 * Lay::BUF, tx + 1, ty + 1);
-    T g[K][Q];
-    CompState<T> cs[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-#pragma unroll
-      for (int i = 0; i < Q; i++) g[k][i] = ld_s<S, T>(v.pop[(k * Q + i) * TX]);
-      cs[k] = comp_state<L, T, RT>(g[k], T(v.ref[k * TX]));
+  for (int c = 1; c <= np - 2; c++) {
+    bool ok = true;
+    if (c == 1) {
+      ok = mbar_wait_bounded(&fld_full[0], 0) && mbar_wait_bounded(&fld_full[1], 0);
     }
-    auto slot_of = [&](int czv) { return czv == 0 ? sl0 : (czv > 0 ? slp : slm); };
-    auto nbr = [&](int fi, int i) -> T {
-      const int sl = slot_of(cz<L>(i));
-      const int e = e0 + cy<L>(i) * EX + cx<L>(i);
-      if (WALLS && msk[sl * NE + e]) return fld[(sl0 * NV + fi) * NE + e0];
-      return fld[(sl * NV + fi) * NE + e];
-    };
-    if constexpr (MODEL == kCG) {
-      const T Fx[3] = {T(0), T(0), T(0)};  // the repulsion force runs on the generic kernel
-      cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
-    } else if constexpr (MODEL == kSCMP) {
-      scmp_collide<L, T>(p, g, cs[0], nbr);
-    } else {
-      sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
-    }
-    const int zz = wrap(z, p.nz), zm = zz == 0 ? p.nz - 1 : zz - 1, zpp = zz + 1 >= p.nz ? 0 : zz + 1;
-    const long long pm = zm * plane_n, p0 = zz * plane_n, pp = zpp * plane_n;
-    const long long n0 = gx + row0 + p0;
-#pragma unroll
-    for (int k = 0; k < K; k++) rout[(long long)k * N + n0] = RT(cs[k].q);
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-      const int dxv = cx<L>(i), dyv = cy<L>(i), dzv = cz<L>(i);
-      const long long X = dxv == 0 ? gx : (dxv > 0 ? xp : xm);
-      const long long Y = dyv == 0 ? row0 : (dyv > 0 ? rowp : rowm);
-      const long long Z = dzv == 0 ? p0 : (dzv > 0 ? pp : pm);
-      long long nd = X + Y + Z;
-      int id = i;
-      const int sl = slot_of(dzv);
-      const int ed = e0 + dyv * EX + dxv;
-      bool bounce = false;
-      if (WALLS && i != 0 && msk[sl * NE + ed]) {
-        nd = n0;
-        id = opp<L>(i);
-        bounce = true;
-      }
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-        T val = g[k][i];
-        if (i != 0 && !bounce) val += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(sl * NV + NF + k) * NE + ed]);
-        fout[(long long)(k * Q + id) * N + nd] = st_s<S, T>(val);
-      }
-    }
-  };
-
-  // prologue: planes z0-1, z0, z0+1 in flight; reduce z0-1, refill its buffer with z0+2
-  if (tid == 0) {
-    issue(z0 - 1);
-    issue(z0);
-    if (z0 + 1 <= z1) issue(z0 + 1);
-  }
-  bool ok = wait_plane(z0 - 1);
-  if (ok) stage_plane(z0 - 1);
-  if (__syncthreads_or(!ok)) {
-    give_up();
-    return;
-  }
-  if (tid == 0 && z0 + 2 <= z1) issue(z0 + 2);
-  ok = wait_plane(z0);
-  if (ok) stage_plane(z0);
-  if (__syncthreads_or(!ok)) {
-    give_up();
-    return;
-  }
-  for (int z = z0; z < z1; z++) {
-    ok = wait_plane(z + 1);
-    if (ok) stage_plane(z + 1);
-    if (__syncthreads_or(!ok)) {
+    ok = ok && mbar_wait_bounded(&fld_full[(c + 1) % kFieldSlots], ((c + 1) / kFieldSlots) & 1);
+    ok = ok && mbar_wait_bounded(&raw_full[c % kRawSlots], (c / kRawSlots) & 1);
+    if (!ok) {
       give_up();
       return;
     }
-    collide(z);
-    __syncthreads();
-    if (tid == 0 && z + 3 <= z1) issue(z + 3);  // refill the buffer plane z used
+    const int slm = (c - 1) % kFieldSlots, sl0 = c % kFieldSlots, slp = (c + 1) % kFieldSlots;
+    const int z = z0 - 1 + c;
+    const bool live = !(WALLS && msk[sl0 * NE + e0]);
+    if (live) {
+      const View v = view(bufs + (c % kRawSlots) * Lay::BUF, tx + 1, ty + 1);
+      T g[K][Q];
+      CompState<T> cs[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+#pragma unroll
+        for (int i = 0; i < Q; i++) g[k][i] = ld_s<S, T>(v.pop[(k * Q + i) * TX]);
+        cs[k] = comp_state<L, T, RT>(g[k], T(v.ref[k * TX]));
+      }
+      auto slot_of = [&](int czv) { return czv == 0 ? sl0 : (czv > 0 ? slp : slm); };
+      auto nbr = [&](int fi, int i) -> T {
+        const int sl = slot_of(cz<L>(i));
+        const int e = e0 + cy<L>(i) * EX + cx<L>(i);
+        if (WALLS && msk[sl * NE + e]) return fld[(sl0 * NV + fi) * NE + e0];
+        return fld[(sl * NV + fi) * NE + e];
+      };
+      if constexpr (MODEL == kCG) {
+        const T Fx[3] = {T(0), T(0), T(0)};  // the repulsion force runs on the generic kernel
+        cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
+      } else if constexpr (MODEL == kSCMP) {
+        scmp_collide<L, T>(p, g, cs[0], nbr);
+      } else {
+        sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
+      }
+      const int zz = wrap(z, p.nz), zm = zz == 0 ? p.nz - 1 : zz - 1, zpp = zz + 1 >= p.nz ? 0 : zz + 1;
+      const long long pm = zm * plane_n, p0 = zz * plane_n, pp = zpp * plane_n;
+      const long long n0 = gx + row0 + p0;
+#pragma unroll
+      for (int k = 0; k < K; k++) rout[(long long)k * N + n0] = RT(cs[k].q);
+#pragma unroll
+      for (int i = 0; i < Q; i++) {
+        const int dxv = cx<L>(i), dyv = cy<L>(i), dzv = cz<L>(i);
+        const long long X = dxv == 0 ? gx : (dxv > 0 ? xp : xm);
+        const long long Y = dyv == 0 ? row0 : (dyv > 0 ? rowp : rowm);
+        const long long Z = dzv == 0 ? p0 : (dzv > 0 ? pp : pm);
+        long long nd = X + Y + Z;
+        int id = i;
+        const int sl = slot_of(dzv);
+        const int ed = e0 + dyv * EX + dxv;
+        bool bounce = false;
+        if (WALLS && i != 0 && msk[sl * NE + ed]) {
+          nd = n0;
+          id = opp<L>(i);
+          bounce = true;
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          T val = g[k][i];
+          if (i != 0 && !bounce) val += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(sl * NV + NF + k) * NE + ed]);
+          fout[(long long)(k * Q + id) * N + nd] = st_s<S, T>(val);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&raw_free[c % kRawSlots]);
+      mbar_arrive(&fld_free[(c - 1) % kFieldSlots]);
+    }
   }
 }
 
