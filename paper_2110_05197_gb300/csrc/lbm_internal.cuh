@@ -104,7 +104,7 @@ StepParams<T> make_step_params(const lbm_ctx* c) {
   s.nx = q.nx;
   s.ny = q.ny;
   s.nz = q.nz;
-  s.tz = c->tz;
+  s.nchunks = (q.nz + c->tz - 1) / c->tz;
   s.n = c->N;
   double phi[2][3];
   rest_weights(q, phi);

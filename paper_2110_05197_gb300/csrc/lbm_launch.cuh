@@ -72,8 +72,8 @@ cudaError_t launch_tma_t(lbm_ctx* c) {
     attr_set = true;
   }
   dim3 block(kTmaThreads, 1, 1);
-  dim3 grid(c->p.nx / TX, c->p.ny / TY, (c->p.nz + c->tz - 1) / c->tz);
   const StepParams<T> sp = make_step_params<T>(c);
+  dim3 grid(c->p.nx / TX, c->p.ny / TY, sp.nchunks);
   S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
   RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
   step_kernel_tma<L, T, S, RT, MODEL, WALLS, TX, TY><<<grid, block, smem, c->stream>>>(
@@ -100,8 +100,8 @@ cudaError_t launch_step_t(lbm_ctx* c) {
     smem_set = smem;
   }
   dim3 block(tx, ty, 1);
-  dim3 grid((c->p.nx + tx - 1) / tx, (c->p.ny + ty - 1) / ty, (c->p.nz + c->tz - 1) / c->tz);
   const StepParams<T> sp = make_step_params<T>(c);
+  dim3 grid((c->p.nx + tx - 1) / tx, (c->p.ny + ty - 1) / ty, sp.nchunks);
   const S* fin = static_cast<const S*>(c->f[c->cur]);
   S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
   const RT* rin = static_cast<const RT*>(c->r[c->cur]);

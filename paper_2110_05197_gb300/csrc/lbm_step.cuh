@@ -48,7 +48,7 @@ enum Model : int { kCG = 0, kSCMP = 1, kSC2C = 2 };
 template <class T>
 struct StepParams {
   int nx, ny, nz;
-  int tz;                 // z planes per block
+  int nchunks;            // z chunks (grid.z); chunk b covers [b*nz/nchunks, (b+1)*nz/nchunks)
   long long n;            // nodes
   T phi[2][3];            // rest-state weights per component and group (CG: Eq. phi; SC: w)
   // CG
@@ -139,14 +139,20 @@ __device__ __forceinline__ void node_fields(const StepParams<T>& p, T s0, T s1, 
   }
 }
 
-// Deviation sum in a fixed order, used for every node so that a node's density is
-// bitwise the same whichever block computes it.
+// Deviation sum over the Q directions as a fixed balanced tree (short dependency chain),
+// used for every node so that a node's density is bitwise the same whichever kernel or
+// block computes it.
+template <int N, class T>
+__device__ __forceinline__ T tree_sum(const T* v) {
+  if constexpr (N == 1) {
+    return v[0];
+  } else {
+    return tree_sum<N / 2, T>(v) + tree_sum<N - N / 2, T>(v + N / 2);
+  }
+}
 template <class L, class T>
 __device__ __forceinline__ T sum_q(const T* v) {
-  T s = v[0];
-#pragma unroll
-  for (int i = 1; i < L::Q; i++) s += v[i];
-  return s;
+  return tree_sum<L::Q, T>(v);
 }
 
 // Per-node density bookkeeping of one component: the stored deviations g (relative to
@@ -448,8 +454,8 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
   const int NE = EX * (TY + 2), NI = TX * TY;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * p.tz;
-  const int z1 = min(z0 + p.tz, p.nz);
+  const int z0 = (int)(((long long)blockIdx.z * p.nz) / p.nchunks);
+  const int z1 = (int)(((long long)(blockIdx.z + 1) * p.nz) / p.nchunks);
   const long long N = p.n;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];

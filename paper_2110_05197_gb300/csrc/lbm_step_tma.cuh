@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * p.tz;
-  const int z1 = min(z0 + p.tz, p.nz);
+  const int z0 = (int)(((long long)blockIdx.z * p.nz) / p.nchunks);
+  const int z1 = (int)(((long long)(blockIdx.z + 1) * p.nz) / p.nchunks);
   const int np = z1 - z0 + 2;  // planes z0-1 .. z1
   const long long N = p.n;
 

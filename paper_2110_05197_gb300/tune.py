@@ -13,8 +13,8 @@ import torch
 
 from . import lbm
 
-CANDIDATES_3D = [(32, 8, 16), (32, 8, 32), (32, 4, 16), (32, 4, 32), (64, 4, 16), (64, 4, 32),
-                 (64, 2, 32), (128, 2, 16), (32, 2, 32), (16, 8, 16)]
+CANDIDATES_3D = [(32, 8, 16), (32, 8, 19), (32, 8, 22), (32, 8, 26), (32, 8, 32), (32, 8, 43), (32, 8, 64),
+                 (32, 4, 16), (32, 4, 32), (64, 4, 16), (64, 4, 32), (128, 2, 16), (16, 8, 16)]
 CANDIDATES_2D = [(32, 8, 1), (32, 4, 1), (64, 4, 1), (128, 2, 1), (256, 1, 1), (64, 2, 1)]
 
 _cache: dict = {}
