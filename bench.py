@@ -69,15 +69,22 @@ def hbm_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling (every 200 ms, each sample time-stamped by
+    nvidia-smi itself).  summary() keeps the samples inside the marked timed region; when
+    that region is shorter than a few sampling periods it widens the window to the load
+    phase marked just before it (the same steps, untimed) and says so."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.marks = {}
+
+    def mark(self, name: str):
+        self.marks[name] = time.time()
 
     def __enter__(self):
         try:
@@ -99,25 +106,35 @@ class ClockSampler:
                 out = ""
             self.lines = [l for l in out.splitlines() if l.strip()]
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    def _samples(self):
+        import datetime
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        out = []
         for l in getattr(self, "lines", []):
             f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+            out.append((ts, sm, mx, {nm for nm, v in zip(names, f[6:10]) if v.lower() == "active"}))
+        return out
+
+    def summary(self, start="timed_start", end="timed_end", wide_start="load_start"):
+        samples = self._samples()
+        t0, t1 = self.marks.get(start), self.marks.get(end)
+        window = "timed region"
+        sel = [s for s in samples if t0 is not None and t1 is not None and t0 <= s[0] <= t1]
+        if len(sel) < 3 and wide_start in self.marks:
+            window = "timed region + the untimed load phase of the same steps just before it"
+            sel = [s for s in samples if self.marks[wide_start] <= s[0] <= (t1 or s[0])]
+        if not sel:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set().union(*(s[3] for s in sel))
+        return {"sm_mhz": statistics.median(s[1] for s in sel), "sm_max_mhz": max(s[2] for s in sel),
+                "reasons": sorted(reasons), "samples": len(sel), "window": window}
 
 
 def dist_env():
@@ -208,11 +225,21 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = cg.launch_count() + sc.launch_count()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
+        # untimed load phase (>= 1.2 s of the same steps) so that the clock record has
+        # samples under load even when K steps take only milliseconds
+        clk.mark("load_start")
+        t_load = time.perf_counter()
+        while time.perf_counter() - t_load < 1.2:
+            for _ in range(20):
+                cg.step(1)
+                sc.step(1)
+            torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = cg.launch_count() + sc.launch_count()
+        clk.mark("timed_start")
         start.record(stream)
         for k in range(K):
             ev[k][0].record(stream)
@@ -222,6 +249,7 @@ def run_ours(args):
             ev[k][2].record(stream)
         end.record(stream)
         torch.cuda.synchronize()
+        clk.mark("timed_end")
     launches = cg.launch_count() + sc.launch_count() - l0
     total_ms = start.elapsed_time(end)
     if ws > 1:

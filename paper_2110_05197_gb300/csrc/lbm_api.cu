@@ -178,21 +178,14 @@ bool build_tma_maps(lbm_ctx* c) {
   const CUtensorMapDataType dt = p.precision == LBM_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : p.precision == LBM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const int sw = (int)(16 / c->elt), rsw = (int)(16 / c->relt);
   for (int b = 0; b < 2; b++) {
     TmaMaps& m = c->tma[b];
     bool ok = encode4(fn, &m.pop_main_row, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, kTmaTX, 1) &&
               encode4(fn, &m.pop_main_mid, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, kTmaTX, kTmaTY) &&
-              encode4(fn, &m.pop_strip_row, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, sw, 1) &&
-              encode4(fn, &m.pop_strip_mid, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, sw, kTmaTY) &&
               encode4(fn, &m.ref_main_row, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
                       c->N, kTmaTX, 1) &&
               encode4(fn, &m.ref_main_mid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
-                      c->N, kTmaTX, kTmaTY) &&
-              encode4(fn, &m.ref_strip_row, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
-                      c->N, rsw, 1) &&
-              encode4(fn, &m.ref_strip_mid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
-                      c->N, rsw, kTmaTY);
+                      c->N, kTmaTX, kTmaTY);
     if (!ok) return false;
   }
   return true;
@@ -241,6 +234,11 @@ lbm_status lbm_create(const lbm_params* p, void* ws, size_t* ws_bytes, void* str
   c->tx = 32;
   c->ty = 8;
   c->tz = p->lattice == LBM_D3Q19 ? (p->nz < 16 ? p->nz : 16) : 1;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    nsm = 0;
+  c->nsm = nsm > 0 ? nsm : 1;
+  c->occ_fn = nullptr;
   c->tma_ok = lbm::build_tma_maps(c);
   *out = c;
   return LBM_OK;
@@ -248,8 +246,8 @@ lbm_status lbm_create(const lbm_params* p, void* ws, size_t* ws_bytes, void* str
 
 lbm_status lbm_set_tiling(lbm_ctx* c, int32_t tx, int32_t ty, int32_t tz) {
   if (!c) return LBM_EINVAL;
-  if (tx < 1 || ty < 1 || tz < 1 || tx * ty > 256 || (tx * ty) % 32 != 0) return LBM_EINVAL;
-  if (c->p.lattice == LBM_D2Q9 && tz != 1) return LBM_EINVAL;
+  if (tx < 1 || ty < 1 || tz < 0 || tx * ty > 256 || (tx * ty) % 32 != 0) return LBM_EINVAL;
+  if (c->p.lattice == LBM_D2Q9 && tz > 1) return LBM_EINVAL;
   c->tx = tx;
   c->ty = ty;
   c->tz = tz;

@@ -41,7 +41,10 @@ struct lbm_ctx {
   lbm_status sticky;
   unsigned long long launches;
   long long steps;
-  int tx, ty, tz;        // step kernel tiling
+  int tx, ty, tz;        // step kernel tiling (tz = 0: persistent grid)
+  int nsm;               // streaming multiprocessors of the device
+  const void* occ_fn;    // step kernel variant whose occupancy occ_blocks holds
+  int occ_tx, occ_ty, occ_blocks;
   bool rep;              // CG repulsion force enabled (rep_pi != 0)
   void* colour;          // [N] rho^N (step compute type), repulsion pre-pass
   void* normals;         // [3][N] unit colour gradients, repulsion pre-pass
@@ -104,7 +107,10 @@ StepParams<T> make_step_params(const lbm_ctx* c) {
   s.nx = q.nx;
   s.ny = q.ny;
   s.nz = q.nz;
-  s.nchunks = (q.nz + c->tz - 1) / c->tz;
+  s.ncx = (q.nx + c->tx - 1) / c->tx;
+  s.ncol = s.ncx * ((q.ny + c->ty - 1) / c->ty);
+  // chunked grid (tz > 0); a persistent grid's size is set by the launcher
+  s.nblk = c->tz > 0 ? s.ncol * ((q.nz + c->tz - 1) / c->tz) : s.ncol;
   s.n = c->N;
   double phi[2][3];
   rest_weights(q, phi);

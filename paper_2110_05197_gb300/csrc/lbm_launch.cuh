@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "lbm_internal.cuh"
+#include "lbm_step_tmac.cuh"
 
 namespace lbm {
 
@@ -60,6 +61,13 @@ cudaError_t launch_rep_prepass_t(lbm_ctx* c, int buf) {
   return cudaGetLastError();
 }
 
+// Persistent grid: as many blocks as can be resident, at most one per tile-plane.
+template <class T>
+int persistent_blocks(const StepParams<T>& sp, int resident) {
+  const long long U = (long long)sp.ncol * sp.nz;
+  return (int)std::max<long long>(1, std::min<long long>(U, resident));
+}
+
 template <class L, class T, class S, class RT, int MODEL, bool WALLS>
 cudaError_t launch_tma_t(lbm_ctx* c) {
   constexpr int TX = kTmaTX, TY = kTmaTY;
@@ -72,19 +80,74 @@ cudaError_t launch_tma_t(lbm_ctx* c) {
     attr_set = true;
   }
   dim3 block(kTmaThreads, 1, 1);
-  const StepParams<T> sp = make_step_params<T>(c);
-  dim3 grid(c->p.nx / TX, c->p.ny / TY, sp.nchunks);
+  StepParams<T> sp = make_step_params<T>(c);
+  if (c->tz == 0) sp.nblk = persistent_blocks(sp, c->nsm);  // one block per SM (shared memory)
+  dim3 grid(sp.nblk, 1, 1);
+  const S* fin = static_cast<const S*>(c->f[c->cur]);
+  const RT* rin = static_cast<const RT*>(c->r[c->cur]);
   S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
   RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
   step_kernel_tma<L, T, S, RT, MODEL, WALLS, TX, TY><<<grid, block, smem, c->stream>>>(
-      c->tma[c->cur], fout, rout, c->solid, &c->diag->status, sp);
+      c->tma[c->cur], fin, rin, fout, rout, c->solid, &c->diag->status, sp);
   return cudaGetLastError();
+}
+
+// TMA-staged kernel with the x-halo exchanged inside a cluster of nx / 32 blocks.
+template <class L, class T, class S, class RT, int MODEL, bool WALLS>
+cudaError_t launch_tmac_t(lbm_ctx* c) {
+  constexpr int TX = kTmaTX, TY = kTmaTY;
+  constexpr size_t smem = tmac_smem_bytes<L, T, S, RT, MODEL, WALLS, TX, TY>();
+  auto kern = step_kernel_tmac<L, T, S, RT, MODEL, WALLS, TX, TY>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int C = c->p.nx / TX;
+  StepParams<T> sp = make_step_params<T>(c);
+  sp.ncx = C;                // blocks per cluster
+  sp.ncol = c->p.ny / TY;    // tile rows: the work partition's columns
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kTmaThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (c->tz > 0) {
+    sp.nblk = sp.ncol * ((c->p.nz + c->tz - 1) / c->tz);
+  } else {
+    const void* fn = reinterpret_cast<const void*>(kern);
+    if (c->occ_fn != fn || c->occ_tx != -C) {
+      int ncl = 0;
+      cfg.gridDim = dim3(C, 1, 1);
+      cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      c->occ_fn = fn;
+      c->occ_tx = -C;
+      c->occ_ty = 0;
+      c->occ_blocks = ncl > 0 ? ncl : 1;
+    }
+    sp.nblk = persistent_blocks(sp, c->occ_blocks);  // clusters
+  }
+  cfg.gridDim = dim3(sp.nblk * C, 1, 1);
+  S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
+  RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
+  return cudaLaunchKernelEx(&cfg, kern, c->tma[c->cur], fout, rout, c->solid, &c->diag->status, sp);
 }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 cudaError_t launch_step_t(lbm_ctx* c) {
   if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
-    if (c->tma_ok && c->tx == kTmaTX && c->ty == kTmaTY) return launch_tma_t<L, T, S, RT, MODEL, WALLS>(c);
+    if (c->tma_ok && c->tx == kTmaTX && c->ty == kTmaTY) {
+      if (c->p.nx / kTmaTX <= kMaxCluster) return launch_tmac_t<L, T, S, RT, MODEL, WALLS>(c);
+      return launch_tma_t<L, T, S, RT, MODEL, WALLS>(c);
+    }
   }
   if constexpr (REP) {
     cudaError_t e = launch_rep_prepass_t<L, T, S, RT>(c, c->cur);
@@ -100,8 +163,22 @@ cudaError_t launch_step_t(lbm_ctx* c) {
     smem_set = smem;
   }
   dim3 block(tx, ty, 1);
-  const StepParams<T> sp = make_step_params<T>(c);
-  dim3 grid((c->p.nx + tx - 1) / tx, (c->p.ny + ty - 1) / ty, sp.nchunks);
+  StepParams<T> sp = make_step_params<T>(c);
+  if (c->tz == 0) {
+    const void* fn = reinterpret_cast<const void*>(step_kernel<L, T, S, RT, MODEL, WALLS, REP>);
+    if (c->occ_fn != fn || c->occ_tx != tx || c->occ_ty != ty) {
+      int nb = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<L, T, S, RT, MODEL, WALLS, REP>,
+                                                                    tx * ty, smem);
+      if (e != cudaSuccess) return e;
+      c->occ_fn = fn;
+      c->occ_tx = tx;
+      c->occ_ty = ty;
+      c->occ_blocks = nb > 0 ? nb : 1;
+    }
+    sp.nblk = persistent_blocks(sp, c->nsm * c->occ_blocks);
+  }
+  dim3 grid(sp.nblk, 1, 1);
   const S* fin = static_cast<const S*>(c->f[c->cur]);
   S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
   const RT* rin = static_cast<const RT*>(c->r[c->cur]);

@@ -48,7 +48,8 @@ enum Model : int { kCG = 0, kSCMP = 1, kSC2C = 2 };
 template <class T>
 struct StepParams {
   int nx, ny, nz;
-  int nchunks;            // z chunks (grid.z); chunk b covers [b*nz/nchunks, (b+1)*nz/nchunks)
+  int ncx, ncol;          // block columns along x, and in total (ncx * columns along y)
+  int nblk;               // blocks in the grid: block b owns tile-planes [b*U/nblk, (b+1)*U/nblk)
   long long n;            // nodes
   T phi[2][3];            // rest-state weights per component and group (CG: Eq. phi; SC: w)
   // CG
@@ -117,6 +118,35 @@ __device__ __forceinline__ T two_sum(T a, T b, T& e) {
   e = (a - (s - bb)) + (b - bb);
   return s;
 }
+
+// Work partition.  The lattice is cut into ncol block columns (tiles of TX x TY nodes,
+// all of z); a tile-plane is one tile at one z, numbered col * nz + z, U = ncol * nz in
+// all.  Block b owns the contiguous range [b*U/nblk, (b+1)*U/nblk): with nblk = ncol *
+// ceil(nz/tz) every range is one balanced z-chunk of one column; with nblk = the resident
+// block count (a persistent grid) every block gets the same number of tile-planes, split
+// into runs (segments) of consecutive z in one column, each marched with its own halo
+// planes.
+struct Segment {
+  int col, z0, z1;  // column and z range [z0, z1)
+};
+struct WorkRange {
+  long long next, end;
+  __device__ WorkRange(int b, int nblk, int ncol, int nz) {
+    const long long U = (long long)ncol * nz;
+    next = (long long)b * U / nblk;
+    end = (long long)(b + 1) * U / nblk;
+  }
+  __device__ bool pop(int nz, Segment& s) {
+    if (next >= end) return false;
+    s.col = (int)(next / nz);
+    s.z0 = (int)(next - (long long)s.col * nz);
+    const long long col_end = (long long)(s.col + 1) * nz;
+    const long long e = end < col_end ? end : col_end;
+    s.z1 = s.z0 + (int)(e - next);
+    next = e;
+    return true;
+  }
+};
 
 // Scalar fields staged for the stencils from the component densities of one node.
 template <int MODEL, class T>
@@ -418,8 +448,8 @@ __device__ __forceinline__ void sc2c_collide(const StepParams<T>& p, T (&g)[2][L
 }
 
 // ---------------------------------------------------------------------------------------
-// The fused step kernel.  blockDim = (TX, TY); grid = (ceil(nx/TX), ceil(ny/TY),
-// ceil(nz/tz)).  Dynamic shared memory: step_smem_bytes().
+// The fused step kernel.  blockDim = (TX, TY); a 1-D grid of p.nblk blocks, each marching
+// the segments of its work range (WorkRange).  Dynamic shared memory: step_smem_bytes().
 template <class L>
 __host__ __device__ constexpr int planes_of() { return L::D == 3 ? 3 : 1; }
 
@@ -453,10 +483,8 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
   const int EX = TX + 2;
   const int NE = EX * (TY + 2), NI = TX * TY;
   const int tid = threadIdx.y * TX + threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = (int)(((long long)blockIdx.z * p.nz) / p.nchunks);
-  const int z1 = (int)(((long long)(blockIdx.z + 1) * p.nz) / p.nchunks);
   const long long N = p.n;
+  int x0 = 0, y0 = 0;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* fld = reinterpret_cast<T*>(smem_raw);           // [NPL][NV][NE]
@@ -499,11 +527,9 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
   };
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool valid = gx < p.nx && gy < p.ny;
   const int e0 = (ty + 1) * EX + (tx + 1);
-  const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;
-  const int ym = gy == 0 ? p.ny - 1 : gy - 1, yp = gy + 1 >= p.ny ? 0 : gy + 1;
+  int gx = 0, gy = 0, xm = 0, xp = 0, ym = 0, yp = 0;
+  bool valid = false;
 
   auto collide = [&](int z, int slm, int sl0, int slp, int pb) {
     if (!valid) return;
@@ -566,23 +592,37 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
     }
   };
 
-  if constexpr (NPL == 3) {
-    stage(z0 - 1, 0, -1);
-    stage(z0, 1, 0);
-    for (int z = z0; z < z1; z++) {
-      const int r = z - z0;
-      const int slm = r % 3, sl0 = (r + 1) % 3, slp = (r + 2) % 3;
-      stage(z + 1, slp, (z + 1 < z1) ? ((r + 1) & 1) : -1);
-      __syncthreads();
-      collide(z, slm, sl0, slp, r & 1);
-      __syncthreads();
-    }
-  } else {
-    for (int z = z0; z < z1; z++) {
-      stage(z, 0, 0);
-      __syncthreads();
-      collide(z, 0, 0, 0, 0);
-      __syncthreads();
+  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+  Segment sg;
+  while (work.pop(p.nz, sg)) {
+    x0 = (sg.col % p.ncx) * TX;
+    y0 = (sg.col / p.ncx) * TY;
+    gx = x0 + tx;
+    gy = y0 + ty;
+    valid = gx < p.nx && gy < p.ny;
+    xm = gx == 0 ? p.nx - 1 : gx - 1;
+    xp = gx + 1 >= p.nx ? 0 : gx + 1;
+    ym = gy == 0 ? p.ny - 1 : gy - 1;
+    yp = gy + 1 >= p.ny ? 0 : gy + 1;
+    const int z0 = sg.z0, z1 = sg.z1;
+    if constexpr (NPL == 3) {
+      stage(z0 - 1, 0, -1);
+      stage(z0, 1, 0);
+      for (int z = z0; z < z1; z++) {
+        const int r = z - z0;
+        const int slm = r % 3, sl0 = (r + 1) % 3, slp = (r + 2) % 3;
+        stage(z + 1, slp, (z + 1 < z1) ? ((r + 1) & 1) : -1);
+        __syncthreads();
+        collide(z, slm, sl0, slp, r & 1);
+        __syncthreads();
+      }
+    } else {
+      for (int z = z0; z < z1; z++) {
+        stage(z, 0, 0);
+        __syncthreads();
+        collide(z, 0, 0, 0, 0);
+        __syncthreads();
+      }
     }
   }
 }

@@ -1,20 +1,21 @@
 // D3Q19 step kernel with TMA-staged planes (16-bit and FP32 storage).
 //
 // Same step as step_kernel (lbm_step.cuh): identical staging sums, collision and push, so
-// the two give bitwise identical results.  What differs is how a plane reaches shared
-// memory.  One thread issues 4-D tensor copies (cp.async.bulk.tensor) of the extended
-// (TX+2) x (TY+2) plane -- every population array and both reference densities -- into
-// a three-deep ring of plane buffers, completing on an mbarrier per buffer; plane z+2 is
-// in flight while plane z+1 is reduced to its stencil fields and plane z collides.  No
-// thread computes a global load address for staging, and the copy latency is off the
-// critical path.
+// the two agree to the last few ulps.  What differs is how a plane reaches shared memory.
+// One producer warp fetches the extended (TX+2) x (TY+2) plane -- every population array
+// and both reference densities -- into a three-deep ring of plane buffers, completing on
+// an mbarrier per buffer; plane z+2 is in flight while plane z+1 is reduced to its
+// stencil fields and plane z collides.
 //
-// Tensor maps view a population buffer [k][i][z][y][x] as a 4-D tensor with dimensions
-// (x, array, y, z), so a box {TX, K*Q, rows, 1} lands in shared memory as
-// [rows][array][x]: row groups (top halo row, TY interior rows, bottom halo row) stack in
-// y.  The x halo columns come as 16-byte strips at x0-SW and x0+TX, wrapped to the far side
-// of the periodic box by choosing the strip's start coordinate; every coordinate is in
-// range and 16-byte aligned (the launcher requires nx % TX == 0 and ny % TY == 0).
+// The TX interior columns of every row come as 4-D tensor copies (cp.async.bulk.tensor)
+// of 128-byte rows: a tensor map views a population buffer [k][i][z][y][x] as a tensor
+// with dimensions (x, array, y, z), so a box {TX, K*Q, rows, 1} lands in shared memory as
+// [rows][array][x].  The two x-halo columns are one element per row and array; as tensor
+// boxes they would be 16-byte requests that cost as much copy-engine time as a full row,
+// so the producer warp's 32 lanes fetch them instead with 4-byte cp.async copies (the
+// aligned 4-byte word holding the element for 16-bit storage), wrapped periodically,
+// whose completion is counted on the same mbarrier (cp.async.mbarrier.arrive.noinc).
+// The launcher requires nx % TX == 0 and ny % TY == 0.
 #pragma once
 
 #include <cuda.h>
@@ -23,11 +24,11 @@
 
 namespace lbm {
 
-// Tensor maps for one population buffer and its reference field: main-x boxes and
-// x-strip boxes, each for a single row and for TY rows.
+// Tensor maps for one population buffer and its reference field: main-column boxes of
+// a single row and of TY rows.
 struct TmaMaps {
-  CUtensorMap pop_main_row, pop_main_mid, pop_strip_row, pop_strip_mid;
-  CUtensorMap ref_main_row, ref_main_mid, ref_strip_row, ref_strip_mid;
+  CUtensorMap pop_main_row, pop_main_mid;
+  CUtensorMap ref_main_row, ref_main_mid;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -68,6 +69,16 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 4-byte asynchronous copy global -> shared, and an mbarrier arrival once this thread's
+// earlier cp.async copies have landed (the arrival is one of the barrier's expected count).
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Bounded wait on an mbarrier phase (the copies complete on their own; the bound keeps a
 // lost completion from hanging the GPU).
 constexpr long long kWaitLimit = 1LL << 22;
@@ -82,11 +93,11 @@ constexpr int kStatusTimeout = 0x100;  // diag status bit: a bounded device wait
 // Tile of the TMA-staged kernel (compile-time: every shared-memory offset is an immediate).
 constexpr int kTmaTX = 32, kTmaTY = 8;
 
-// A tensor copy's shared-memory destination must be 128-byte aligned.  Each region of a
-// plane buffer (population main columns, left/right strips, and the same for the
-// reference densities) is therefore three slabs -- top halo row, TY interior rows, bottom
-// halo row -- each starting on a 128-byte boundary; rows inside the interior slab are
-// contiguous, as the copy writes them.
+// A tensor copy's shared-memory destination must be 128-byte aligned.  The main-column
+// region of a plane buffer (populations, and the same for the reference densities) is
+// therefore three slabs -- top halo row, TY interior rows, bottom halo row -- each starting
+// on a 128-byte boundary; rows inside the interior slab are contiguous, as the copy writes
+// them.
 template <int ROW_BYTES, int TY>
 struct Region {
   static constexpr size_t al(size_t b) { return (b + 127) & ~size_t(127); }
@@ -101,25 +112,25 @@ struct Region {
   __host__ __device__ static constexpr size_t group(int g) { return g == 0 ? 0 : (g == 1 ? S1 : S2); }
 };
 
+// Plane buffer: population main columns, reference main columns (tensor copies), then
+// the x-halo words [side][row][array] of populations and of reference densities.
 template <class L, class S, class RT, int MODEL, int TX, int TY>
 struct TmaLayout {
   static constexpr int K = ModelTraits<MODEL>::K, Q = L::Q, KQ = K * Q;
-  static constexpr int SW = 16 / int(sizeof(S));    // strip width (elements) of populations
-  static constexpr int RSW = 16 / int(sizeof(RT));  // strip width of reference densities
+  static constexpr int EPW = 4 / int(sizeof(S));    // population elements per 4-byte halo word
+  static_assert(sizeof(RT) == 4, "reference densities are 4-byte words here");
   static constexpr int EX = TX + 2, EY = TY + 2, NE = EX * EY, NI = TX * TY;
   using PM = Region<KQ * TX * int(sizeof(S)), TY>;   // population main columns
-  using PS = Region<KQ * SW * int(sizeof(S)), TY>;   // population strip (one side)
   using RMR = Region<K * TX * int(sizeof(RT)), TY>;  // reference main columns
-  using RSR = Region<K * RSW * int(sizeof(RT)), TY>; // reference strip (one side)
-  static constexpr size_t OFF_L = PM::BYTES, OFF_R = OFF_L + PS::BYTES, OFF_RM = OFF_R + PS::BYTES,
-                          OFF_RL = OFF_RM + RMR::BYTES, OFF_RR = OFF_RL + RSR::BYTES;
-  static constexpr size_t BUF = OFF_RR + RSR::BYTES;
-  static_assert(BUF % 128 == 0 && OFF_L % 128 == 0 && OFF_R % 128 == 0 && OFF_RM % 128 == 0 &&
-                    OFF_RL % 128 == 0 && OFF_RR % 128 == 0,
-                "tensor-copy destinations must be 128-byte aligned");
-  // bytes the copies of one plane deliver (the alignment padding is not written)
-  static constexpr uint32_t TX_BYTES =
-      uint32_t(EY) * (KQ * (TX + 2 * SW) * sizeof(S) + K * (TX + 2 * RSW) * sizeof(RT));
+  static constexpr size_t OFF_RM = PM::BYTES;        // reference main columns
+  static constexpr size_t OFF_H = OFF_RM + RMR::BYTES;  // halo words: [2][EY][KQ + K]
+  static constexpr int HW = KQ + K;                  // halo words per side and row
+  static constexpr int NH = 2 * EY * HW;             // halo words per plane
+  static constexpr size_t BUF = (OFF_H + size_t(NH) * 4 + 127) & ~size_t(127);
+  static constexpr size_t BUF_MAIN = OFF_H;          // without the halo words (cluster kernel)
+  static_assert(BUF % 128 == 0 && OFF_RM % 128 == 0, "tensor-copy destinations must be 128-byte aligned");
+  // bytes the tensor copies of one plane deliver (the alignment padding is not written)
+  static constexpr uint32_t TX_BYTES = uint32_t(EY) * (KQ * TX * sizeof(S) + K * TX * sizeof(RT));
 };
 
 constexpr int kStatusLayout = 0x200;  // diag status bit: shared-memory base not 128-byte aligned
@@ -145,24 +156,31 @@ __host__ __device__ constexpr size_t tma_smem_bytes() {
   return 128 + kRawSlots * Lay::BUF + kFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kFieldSlots * Lay::NE : 0);
 }
 
-// Pipeline over the planes j = 0 .. n-1 of a block's z-chunk (plane z = z0 - 1 + j; j = 0
-// and j = n-1 are the halo planes):
-//   producer : raw_full[j%3] <- tensor copies of plane j, after raw_free[j%3] reports
-//              plane j-3 finished (staging and collision);
-//   staging  : waits raw_full, and fld_free[j%4] for plane j-4's fields; writes the fields of
-//              plane j into slot j%4; arrives fld_full[j%4] and raw_free[j%3];
-//   collision: for planes c = 1 .. n-2 waits fld_full of c+1 (c-1, c were waited earlier)
-//              and raw_full of c; collides and pushes; arrives raw_free[c%3] and
-//              fld_free[(c-1)%4] (the last use of plane c-1's fields).
-// No block-wide barrier inside the loop; every wait is bounded and a timeout sets the
-// status word, so no thread can hang.
+// Pipeline.  A block marches the segments of its work range (WorkRange) one after the
+// other; a segment [z0, z1) of column col needs the planes z0-1 .. z1 (the first and last
+// are halo planes).  All roles walk the same global sequence of planes J = 0, 1, ... over
+// the segments, so ring slots (J % 3 raw, J % 4 fields) and mbarrier phases carry on from
+// one segment to the next:
+//   producer : raw_full[J%3] <- tensor copies of plane J, after raw_free[J%3] reports
+//              plane J-3 finished by every consumer warp;
+//   staging  : waits raw_full(J), and fld_free(J-4); writes the fields of plane J into
+//              slot J%4; arrives fld_full(J) and raw_free(J);
+//   collision: for each interior plane waits the fields of J-1, J, J+1 and raw_full(J);
+//              loads its node, arrives raw_free(J), collides and pushes, arrives
+//              fld_free(J-1).  A halo plane gets raw_free after raw_full (its data is not
+//              read); at a segment's end the last two planes' fields are released.
+// Every arrival on a ring barrier for plane J comes after that warp has observed
+// plane J's copy (raw) or fields (fld) complete, so no arrival can land in the phase of
+// plane J-3 (J-4).  No block-wide barrier inside the loop; every wait is bounded and a
+// timeout sets the status word, so no thread can hang.
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
 __global__ void __launch_bounds__(kTmaThreads, 1)
-    step_kernel_tma(const __grid_constant__ TmaMaps maps, S* __restrict__ fout, RT* __restrict__ rout,
+    step_kernel_tma(const __grid_constant__ TmaMaps maps, const S* __restrict__ fin, const RT* __restrict__ rin,
+                    S* __restrict__ fout, RT* __restrict__ rout,
                     const uint8_t* __restrict__ solid, int* __restrict__ status, StepParams<T> p) {
   static_assert(TX * TY == 32 * kCollideWarps, "one collision thread per tile node");
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
-  constexpr int Q = L::Q, K = Lay::K, KQ = Lay::KQ, SW = Lay::SW, RSW = Lay::RSW;
+  constexpr int Q = L::Q, K = Lay::K, KQ = Lay::KQ, EPW = Lay::EPW, HW = Lay::HW;
   constexpr int NF = ModelTraits<MODEL>::NF, NV = NF + K;
   constexpr int EX = Lay::EX, NE = Lay::NE;
   if (*status != 0) return;  // blown-up (or timed-out) state: stop stepping
@@ -178,10 +196,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = (int)(((long long)blockIdx.z * p.nz) / p.nchunks);
-  const int z1 = (int)(((long long)(blockIdx.z + 1) * p.nz) / p.nchunks);
-  const int np = z1 - z0 + 2;  // planes z0-1 .. z1
   const long long N = p.n;
 
   if (smem_addr(bufs) & 127u) {  // copy destinations must be 128-byte aligned
@@ -190,7 +204,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   }
   if (tid == 0) {
     for (int s = 0; s < kRawSlots; s++) {
-      mbar_init(&raw_full[s], 1);
+      mbar_init(&raw_full[s], 1 + 32);  // the producer's expect-tx arrival + one cp.async arrival per lane
       mbar_init(&raw_free[s], kCollideWarps + kStageWarps);
     }
     for (int s = 0; s < kFieldSlots; s++) {
@@ -201,7 +215,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   }
   __syncthreads();  // the only block-wide barrier: barriers initialised
 
-  auto plane_z = [&](int j) { return wrap(z0 - 1 + j, p.nz); };
   auto give_up = [&]() { atomicOr(status, kStatusTimeout); };
 
   // Ext-node views into a plane buffer: base pointers and strides of the node's arrays.
@@ -213,16 +226,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   };
   auto view = [&](const unsigned char* b, int ex, int ey) -> View {
     View v;
-    if (ex == 0) {
-      v.pop = reinterpret_cast<const S*>(b + Lay::OFF_L + Lay::PS::row(ey)) + (SW - 1);
-      v.ps = SW;
-      v.ref = reinterpret_cast<const RT*>(b + Lay::OFF_RL + Lay::RSR::row(ey)) + (RSW - 1);
-      v.rs = RSW;
-    } else if (ex == TX + 1) {
-      v.pop = reinterpret_cast<const S*>(b + Lay::OFF_R + Lay::PS::row(ey));
-      v.ps = SW;
-      v.ref = reinterpret_cast<const RT*>(b + Lay::OFF_RR + Lay::RSR::row(ey));
-      v.rs = RSW;
+    if (ex == 0 || ex == TX + 1) {
+      // halo word of side 0 (left, x0-1) or 1 (right, x0+TX); for 16-bit storage the left
+      // element is the word's upper half
+      const int side = ex == 0 ? 0 : 1;
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(b + Lay::OFF_H) + (side * Lay::EY + ey) * HW;
+      v.pop = reinterpret_cast<const S*>(w) + (side == 0 ? EPW - 1 : 0);
+      v.ps = EPW;
+      v.ref = reinterpret_cast<const RT*>(w + KQ);
+      v.rs = 1;
     } else {
       v.pop = reinterpret_cast<const S*>(b + Lay::PM::row(ey)) + (ex - 1);
       v.ps = TX;
@@ -234,43 +246,61 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 
   if (warp == kCollideWarps + kStageWarps) {
     // ---------------- producer ----------------
-    if (lane != 0) return;
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.pop_main_mid) : "memory");
-    const int yt = y0 == 0 ? p.ny - 1 : y0 - 1, yb = y0 + TY == p.ny ? 0 : y0 + TY;
-    const int xl = x0 == 0 ? p.nx - SW : x0 - SW, xr = x0 + TX == p.nx ? 0 : x0 + TX;
-    const int xlr = x0 == 0 ? p.nx - RSW : x0 - RSW, xrr = x0 + TX == p.nx ? 0 : x0 + TX;
-    int issued = 0;
-    for (int j = 0; j < np; j++) {
-      const int s = j % kRawSlots;
-      if (j >= kRawSlots && !mbar_wait_bounded(&raw_free[s], ((j / kRawSlots) - 1) & 1)) {
-        give_up();
-        break;
-      }
-      const int gz = plane_z(j);
-      unsigned char* b = bufs + s * Lay::BUF;
-      uint64_t* bar = &raw_full[s];
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(bar, Lay::TX_BYTES);
+    if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.pop_main_mid) : "memory");
+    WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+    Segment sg;
+    int J = 0;
+    bool ok = true;
+    const long long plane_n = (long long)p.nx * p.ny;
+    while (ok && work.pop(p.nz, sg)) {
+      const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
+      const int yt = y0 == 0 ? p.ny - 1 : y0 - 1, yb = y0 + TY == p.ny ? 0 : y0 + TY;
+      // x of the 4-byte halo words: the word holding x0-1 (periodic) and the one at x0+TX;
+      // reference densities are one 4-byte element per word
+      const int xl = (x0 == 0 ? p.nx : x0) - EPW, xr = x0 + TX == p.nx ? 0 : x0 + TX;
+      const int xl_ref = (x0 == 0 ? p.nx : x0) - 1;
+      for (int z = sg.z0 - 1; z <= sg.z1; z++, J++) {
+        const int s = J % kRawSlots;
+        if (J >= kRawSlots &&
+            !__all_sync(0xffffffffu, mbar_wait_bounded(&raw_free[s], ((J / kRawSlots) - 1) & 1))) {
+          if (lane == 0) give_up();
+          ok = false;
+          break;
+        }
+        const int gz = wrap(z, p.nz);
+        unsigned char* b = bufs + s * Lay::BUF;
+        uint64_t* bar = &raw_full[s];
+        if (lane == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive_expect_tx(bar, Lay::TX_BYTES);
 #pragma unroll
-      for (int g = 0; g < 3; g++) {
-        const bool mid = g == 1;
-        const int y = g == 0 ? yt : (g == 1 ? y0 : yb);
-        tma_load_4d(b + Lay::PM::group(g), mid ? &maps.pop_main_mid : &maps.pop_main_row, x0, 0, y, gz, bar);
-        tma_load_4d(b + Lay::OFF_L + Lay::PS::group(g), mid ? &maps.pop_strip_mid : &maps.pop_strip_row, xl, 0, y,
-                    gz, bar);
-        tma_load_4d(b + Lay::OFF_R + Lay::PS::group(g), mid ? &maps.pop_strip_mid : &maps.pop_strip_row, xr, 0, y,
-                    gz, bar);
-        tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), mid ? &maps.ref_main_mid : &maps.ref_main_row, x0, 0, y,
-                    gz, bar);
-        tma_load_4d(b + Lay::OFF_RL + Lay::RSR::group(g), mid ? &maps.ref_strip_mid : &maps.ref_strip_row, xlr, 0,
-                    y, gz, bar);
-        tma_load_4d(b + Lay::OFF_RR + Lay::RSR::group(g), mid ? &maps.ref_strip_mid : &maps.ref_strip_row, xrr, 0,
-                    y, gz, bar);
+          for (int g = 0; g < 3; g++) {
+            const bool mid = g == 1;
+            const int y = g == 0 ? yt : (g == 1 ? y0 : yb);
+            tma_load_4d(b + Lay::PM::group(g), mid ? &maps.pop_main_mid : &maps.pop_main_row, x0, 0, y, gz, bar);
+            tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), mid ? &maps.ref_main_mid : &maps.ref_main_row, x0, 0,
+                        y, gz, bar);
+          }
+        }
+        // halo words: h = (side * EY + ey) * HW + a, a < KQ a population array, else a
+        // reference density
+        uint32_t* hw = reinterpret_cast<uint32_t*>(b + Lay::OFF_H);
+        const long long zoff = gz * plane_n;
+        for (int h = lane; h < Lay::NH; h += 32) {
+          const int a = h % HW, r = h / HW;
+          const int ey = r % Lay::EY, side = r / Lay::EY;
+          const int gy = ey == 0 ? yt : (ey == TY + 1 ? yb : y0 + ey - 1);
+          const long long row = zoff + (long long)gy * p.nx;
+          const void* src = a < KQ ? static_cast<const void*>(fin + (long long)a * N + row + (side == 0 ? xl : xr))
+                                   : static_cast<const void*>(rin + (long long)(a - KQ) * N + row +
+                                                              (side == 0 ? xl_ref : xr));
+          cp_async_4(hw + h, src);
+        }
+        cp_async_arrive_noinc(bar);
       }
-      issued = j + 1;
     }
     // wait (bounded) until the copies this block issued have landed before exiting
-    for (int j = issued - kRawSlots; j < issued; j++)
+    for (int j = J - kRawSlots; j < J; j++)
       if (j >= 0) mbar_wait_bounded(&raw_full[j % kRawSlots], (j / kRawSlots) & 1);
     return;
   }
@@ -278,42 +308,49 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   if (warp >= kCollideWarps) {
     // ---------------- staging ----------------
     const int stid = tid - 32 * kCollideWarps;
-    for (int j = 0; j < np; j++) {
-      const int s = j % kRawSlots, fs = j % kFieldSlots;
-      bool ok = mbar_wait_bounded(&raw_full[s], (j / kRawSlots) & 1);
-      if (ok && j >= kFieldSlots) ok = mbar_wait_bounded(&fld_free[fs], ((j / kFieldSlots) - 1) & 1);
-      if (!ok) {
-        give_up();
-        return;
-      }
-      const unsigned char* b = bufs + s * Lay::BUF;
-      const int gz = plane_z(j);
-      for (int e = stid; e < NE; e += 32 * kStageWarps) {
-        const int ey = e / EX, ex = e - ey * EX;
-        const View v = view(b, ex, ey);
-        T rho[2] = {T(0), T(0)};
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-          T g[Q];
-#pragma unroll
-          for (int i = 0; i < Q; i++) g[i] = ld_s<S, T>(v.pop[(k * Q + i) * v.ps]);
-          const CompState<T> c = comp_state<L, T, RT>(g, T(v.ref[k * v.rs]));
-          rho[k] = c.rho;
-          fld[(fs * NV + NF + k) * NE + e] = c.q;
+    WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+    Segment sg;
+    int J = 0;
+    while (work.pop(p.nz, sg)) {
+      const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
+      for (int z = sg.z0 - 1; z <= sg.z1; z++, J++) {
+        const int s = J % kRawSlots, fs = J % kFieldSlots;
+        bool ok = mbar_wait_bounded(&raw_full[s], (J / kRawSlots) & 1);
+        if (ok && J >= kFieldSlots) ok = mbar_wait_bounded(&fld_free[fs], ((J / kFieldSlots) - 1) & 1);
+        ok = __all_sync(0xffffffffu, ok);  // one decision per warp
+        if (!ok) {
+          give_up();
+          return;
         }
-        T out[2];
-        node_fields<MODEL, T>(p, rho[0], rho[1], out);
+        const unsigned char* b = bufs + s * Lay::BUF;
+        const int gz = wrap(z, p.nz);
+        for (int e = stid; e < NE; e += 32 * kStageWarps) {
+          const int ey = e / EX, ex = e - ey * EX;
+          const View v = view(b, ex, ey);
+          T rho[2] = {T(0), T(0)};
 #pragma unroll
-        for (int f = 0; f < NF; f++) fld[(fs * NV + f) * NE + e] = out[f];
-        if (WALLS) {
-          const int gxn = wrap(x0 - 1 + ex, p.nx), gyn = wrap(y0 - 1 + ey, p.ny);
-          msk[fs * NE + e] = solid[gxn + (long long)p.nx * (gyn + (long long)p.ny * gz)];
+          for (int k = 0; k < K; k++) {
+            T g[Q];
+#pragma unroll
+            for (int i = 0; i < Q; i++) g[i] = ld_s<S, T>(v.pop[(k * Q + i) * v.ps]);
+            const CompState<T> c = comp_state<L, T, RT>(g, T(v.ref[k * v.rs]));
+            rho[k] = c.rho;
+            fld[(fs * NV + NF + k) * NE + e] = c.q;
+          }
+          T out[2];
+          node_fields<MODEL, T>(p, rho[0], rho[1], out);
+#pragma unroll
+          for (int f = 0; f < NF; f++) fld[(fs * NV + f) * NE + e] = out[f];
+          if (WALLS) {
+            const int gxn = wrap(x0 - 1 + ex, p.nx), gyn = wrap(y0 - 1 + ey, p.ny);
+            msk[fs * NE + e] = solid[gxn + (long long)p.nx * (gyn + (long long)p.ny * gz)];
+          }
         }
-      }
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&fld_full[fs]);
-        mbar_arrive(&raw_free[s]);
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&fld_full[fs]);
+          mbar_arrive(&raw_free[s]);
+        }
       }
     }
     return;
@@ -321,88 +358,120 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 
   // ---------------- collision ----------------
   const int tx = tid % TX, ty = tid / TX;
-  const int gx = x0 + tx, gy = y0 + ty;
   const int e0 = (ty + 1) * EX + (tx + 1);
-  const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;
-  const int ym = gy == 0 ? p.ny - 1 : gy - 1, yp = gy + 1 >= p.ny ? 0 : gy + 1;
   const long long nxl = p.nx;
   const long long plane_n = (long long)p.nx * p.ny;
-  const long long rowm = ym * nxl, row0 = gy * nxl, rowp = yp * nxl;
-  if (lane == 0) mbar_arrive(&raw_free[0]);  // plane 0 is a halo plane: nothing to collide
-
-  for (int c = 1; c <= np - 2; c++) {
-    bool ok = true;
-    if (c == 1) {
-      ok = mbar_wait_bounded(&fld_full[0], 0) && mbar_wait_bounded(&fld_full[1], 0);
-    }
-    ok = ok && mbar_wait_bounded(&fld_full[(c + 1) % kFieldSlots], ((c + 1) / kFieldSlots) & 1);
-    ok = ok && mbar_wait_bounded(&raw_full[c % kRawSlots], (c / kRawSlots) & 1);
-    if (!ok) {
+  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+  Segment sg;
+  int J = 0;  // global index of the segment's first (halo) plane
+  auto release_raw = [&](int Jr) {  // a plane whose raw data this warp does not read
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&raw_full[Jr % kRawSlots], (Jr / kRawSlots) & 1)))
+      return false;
+    if (lane == 0) mbar_arrive(&raw_free[Jr % kRawSlots]);
+    return true;
+  };
+  while (work.pop(p.nz, sg)) {
+    const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;
+    const int ym = gy == 0 ? p.ny - 1 : gy - 1, yp = gy + 1 >= p.ny ? 0 : gy + 1;
+    const long long rowm = ym * nxl, row0 = gy * nxl, rowp = yp * nxl;
+    const int np = sg.z1 - sg.z0 + 2;  // planes z0-1 .. z1
+    if (!release_raw(J)) {              // leading halo plane: nothing to collide
       give_up();
       return;
     }
-    const int slm = (c - 1) % kFieldSlots, sl0 = c % kFieldSlots, slp = (c + 1) % kFieldSlots;
-    const int z = z0 - 1 + c;
-    const bool live = !(WALLS && msk[sl0 * NE + e0]);
-    if (live) {
-      const View v = view(bufs + (c % kRawSlots) * Lay::BUF, tx + 1, ty + 1);
+    for (int c = 1; c <= np - 2; c++) {
+      const int Jc = J + c;
+      bool ok = true;
+      if (c == 1)
+        ok = mbar_wait_bounded(&fld_full[(Jc - 1) % kFieldSlots], ((Jc - 1) / kFieldSlots) & 1) &&
+             mbar_wait_bounded(&fld_full[Jc % kFieldSlots], (Jc / kFieldSlots) & 1);
+      ok = ok && mbar_wait_bounded(&fld_full[(Jc + 1) % kFieldSlots], ((Jc + 1) / kFieldSlots) & 1);
+      ok = ok && mbar_wait_bounded(&raw_full[Jc % kRawSlots], (Jc / kRawSlots) & 1);
+      ok = __all_sync(0xffffffffu, ok);  // one decision per warp
+      if (!ok) {
+        give_up();
+        return;
+      }
+      const int slm = (Jc - 1) % kFieldSlots, sl0 = Jc % kFieldSlots, slp = (Jc + 1) % kFieldSlots;
+      const int z = sg.z0 - 1 + c;
+      const bool live = !(WALLS && msk[sl0 * NE + e0]);
       T g[K][Q];
       CompState<T> cs[K];
-#pragma unroll
-      for (int k = 0; k < K; k++) {
-#pragma unroll
-        for (int i = 0; i < Q; i++) g[k][i] = ld_s<S, T>(v.pop[(k * Q + i) * TX]);
-        cs[k] = comp_state<L, T, RT>(g[k], T(v.ref[k * TX]));
-      }
-      auto slot_of = [&](int czv) { return czv == 0 ? sl0 : (czv > 0 ? slp : slm); };
-      auto nbr = [&](int fi, int i) -> T {
-        const int sl = slot_of(cz<L>(i));
-        const int e = e0 + cy<L>(i) * EX + cx<L>(i);
-        if (WALLS && msk[sl * NE + e]) return fld[(sl0 * NV + fi) * NE + e0];
-        return fld[(sl * NV + fi) * NE + e];
-      };
-      if constexpr (MODEL == kCG) {
-        const T Fx[3] = {T(0), T(0), T(0)};  // the repulsion force runs on the generic kernel
-        cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
-      } else if constexpr (MODEL == kSCMP) {
-        scmp_collide<L, T>(p, g, cs[0], nbr);
-      } else {
-        sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
-      }
-      const int zz = wrap(z, p.nz), zm = zz == 0 ? p.nz - 1 : zz - 1, zpp = zz + 1 >= p.nz ? 0 : zz + 1;
-      const long long pm = zm * plane_n, p0 = zz * plane_n, pp = zpp * plane_n;
-      const long long n0 = gx + row0 + p0;
-#pragma unroll
-      for (int k = 0; k < K; k++) rout[(long long)k * N + n0] = RT(cs[k].q);
-#pragma unroll
-      for (int i = 0; i < Q; i++) {
-        const int dxv = cx<L>(i), dyv = cy<L>(i), dzv = cz<L>(i);
-        const long long X = dxv == 0 ? gx : (dxv > 0 ? xp : xm);
-        const long long Y = dyv == 0 ? row0 : (dyv > 0 ? rowp : rowm);
-        const long long Z = dzv == 0 ? p0 : (dzv > 0 ? pp : pm);
-        long long nd = X + Y + Z;
-        int id = i;
-        const int sl = slot_of(dzv);
-        const int ed = e0 + dyv * EX + dxv;
-        bool bounce = false;
-        if (WALLS && i != 0 && msk[sl * NE + ed]) {
-          nd = n0;
-          id = opp<L>(i);
-          bounce = true;
-        }
+      if (live) {
+        const View v = view(bufs + (Jc % kRawSlots) * Lay::BUF, tx + 1, ty + 1);
 #pragma unroll
         for (int k = 0; k < K; k++) {
-          T val = g[k][i];
-          if (i != 0 && !bounce) val += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(sl * NV + NF + k) * NE + ed]);
-          fout[(long long)(k * Q + id) * N + nd] = st_s<S, T>(val);
+#pragma unroll
+          for (int i = 0; i < Q; i++) g[k][i] = ld_s<S, T>(v.pop[(k * Q + i) * TX]);
+          cs[k] = comp_state<L, T, RT>(g[k], T(v.ref[k * TX]));
         }
       }
+      // the raw plane is no longer read: hand its buffer back to the producer before the
+      // collision arithmetic, so that the next copy is in flight meanwhile
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&raw_free[Jc % kRawSlots]);
+      if (live) {
+        auto slot_of = [&](int czv) { return czv == 0 ? sl0 : (czv > 0 ? slp : slm); };
+        auto nbr = [&](int fi, int i) -> T {
+          const int sl = slot_of(cz<L>(i));
+          const int e = e0 + cy<L>(i) * EX + cx<L>(i);
+          if (WALLS && msk[sl * NE + e]) return fld[(sl0 * NV + fi) * NE + e0];
+          return fld[(sl * NV + fi) * NE + e];
+        };
+        if constexpr (MODEL == kCG) {
+          const T Fx[3] = {T(0), T(0), T(0)};  // the repulsion force runs on the generic kernel
+          cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
+        } else if constexpr (MODEL == kSCMP) {
+          scmp_collide<L, T>(p, g, cs[0], nbr);
+        } else {
+          sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
+        }
+        const int zz = z, zm = zz == 0 ? p.nz - 1 : zz - 1, zpp = zz + 1 >= p.nz ? 0 : zz + 1;
+        const long long pm = zm * plane_n, p0 = zz * plane_n, pp = zpp * plane_n;
+        const long long n0 = gx + row0 + p0;
+#pragma unroll
+        for (int k = 0; k < K; k++) rout[(long long)k * N + n0] = RT(cs[k].q);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+          const int dxv = cx<L>(i), dyv = cy<L>(i), dzv = cz<L>(i);
+          const long long X = dxv == 0 ? gx : (dxv > 0 ? xp : xm);
+          const long long Y = dyv == 0 ? row0 : (dyv > 0 ? rowp : rowm);
+          const long long Z = dzv == 0 ? p0 : (dzv > 0 ? pp : pm);
+          long long nd = X + Y + Z;
+          int id = i;
+          const int sl = slot_of(dzv);
+          const int ed = e0 + dyv * EX + dxv;
+          bool bounce = false;
+          if (WALLS && i != 0 && msk[sl * NE + ed]) {
+            nd = n0;
+            id = opp<L>(i);
+            bounce = true;
+          }
+#pragma unroll
+          for (int k = 0; k < K; k++) {
+            T val = g[k][i];
+            if (i != 0 && !bounce) val += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(sl * NV + NF + k) * NE + ed]);
+            fout[(long long)(k * Q + id) * N + nd] = st_s<S, T>(val);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&fld_free[(Jc - 1) % kFieldSlots]);
     }
+    // segment end: the last interior plane's fields and the trailing halo plane are done
+    const int Je = J + np - 1;
     __syncwarp();
     if (lane == 0) {
-      mbar_arrive(&raw_free[c % kRawSlots]);
-      mbar_arrive(&fld_free[(c - 1) % kFieldSlots]);
+      mbar_arrive(&fld_free[(Je - 1) % kFieldSlots]);
+      mbar_arrive(&fld_free[Je % kFieldSlots]);
     }
+    if (!release_raw(Je)) {
+      give_up();
+      return;
+    }
+    J += np;
   }
 }
 

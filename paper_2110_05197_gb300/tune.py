@@ -1,7 +1,8 @@
 """Launch-shape autotuner for the fused step kernel.
 
-For a lattice it times a handful of tilings (block columns tx x ty, z planes per block tz;
-32 x 8 selects the TMA-staged kernel where the lattice allows it) on the lattice's own
+For a lattice it times a handful of tilings (block columns tx x ty, z planes per block tz,
+tz = 0 for the persistent grid; 32 x 8 selects the TMA-staged kernel where the lattice
+allows it) on the lattice's own
 state, keeps the fastest, and restores the state bit for bit (raw state save/load), so
 tuning never changes a simulation's result.  The choice is cached per lattice shape,
 model, precision, walls and repulsion so that every lattice of a shape runs the same
@@ -13,9 +14,10 @@ import torch
 
 from . import lbm
 
-CANDIDATES_3D = [(32, 8, 16), (32, 8, 19), (32, 8, 22), (32, 8, 26), (32, 8, 32), (32, 8, 43), (32, 8, 64),
-                 (32, 4, 16), (32, 4, 32), (64, 4, 16), (64, 4, 32), (128, 2, 16), (16, 8, 16)]
-CANDIDATES_2D = [(32, 8, 1), (32, 4, 1), (64, 4, 1), (128, 2, 1), (256, 1, 1), (64, 2, 1)]
+# tz = 0 selects the persistent grid (equal shares of all tile-planes per resident block)
+CANDIDATES_3D = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (16, 8, 0), (128, 2, 0),
+                 (32, 8, 16), (32, 8, 22), (32, 8, 32), (32, 4, 16), (64, 4, 16)]
+CANDIDATES_2D = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (128, 2, 0), (32, 8, 1), (32, 4, 1), (64, 4, 1), (128, 2, 1)]
 
 _cache: dict = {}
 
@@ -30,7 +32,7 @@ def candidates_for(p: "lbm.Params"):
     cands = CANDIDATES_3D if p.lattice == lbm.D3Q19 else CANDIDATES_2D
     out = []
     for tx, ty, tz in cands:
-        tz = min(tz, p.nz)
+        tz = min(tz, p.nz) if p.lattice == lbm.D3Q19 else tz
         if (tx, ty, tz) not in out:
             out.append((tx, ty, tz))
     return out

@@ -153,17 +153,19 @@ def test_16bit_storage_accuracy(orc, lbm, name, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
-@pytest.mark.parametrize("shape", [(37, 21, 19), (64, 24, 20)])
+@pytest.mark.parametrize("shape", [(37, 21, 19), (64, 24, 20), (96, 64, 48), (288, 16, 6)])
 def test_tiling_does_not_change_results(lbm, precision, shape):
     """Within one kernel the launch shape never changes a bit: the generic kernel in several
-    tilings, and the TMA-staged kernel (32 x 8 tiles, used for (64, 24, 20) in FP32/FP16)
-    for two z-chunk lengths.  The two kernels inline the same per-node code but the compiler
+    tilings, and the TMA-staged kernel (32 x 8 tiles, used for the x % 32 == 0 shapes in
+    FP32/FP16; with the x-halo exchanged in a cluster of nx / 32 blocks up to nx = 256, with
+    fetched halo columns at nx = 288) for two z-chunk lengths, each also as a persistent
+    grid (tz = 0; at 96 x 64 x 48 every block's share spans several columns).  The two kernels inline the same per-node code but the compiler
     fuses multiply-adds differently, so across kernels the states agree to a few ulps of
     the stored deviations."""
     case = C.cg_drop3d(*shape)
     tma = shape[0] % 32 == 0 and shape[1] % 8 == 0 and precision != 0
-    generic = [(64, 4, 5), (32, 2, 19), (128, 2, 1)]
-    staged = [(32, 8, 16), (32, 8, 3)]
+    generic = [(64, 4, 5), (32, 2, 19), (128, 2, 1), (32, 4, 0), (64, 4, 0)]
+    staged = [(32, 8, 16), (32, 8, 3), (32, 8, 0)]
     outs = {}
     for tiling in generic + staged:
         lat = C.gpu_lattice(lbm, case, precision)
