@@ -145,7 +145,8 @@ template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 cudaError_t launch_step_t(lbm_ctx* c) {
   if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
     if (c->tma_ok && c->tx == kTmaTX && c->ty == kTmaTY) {
-      if (c->p.nx / kTmaTX <= kMaxCluster) return launch_tmac_t<L, T, S, RT, MODEL, WALLS>(c);
+      if (c->p.nx / kTmaTX <= kMaxCluster && (long long)c->K * c->Q * c->N < (1LL << 31))
+        return launch_tmac_t<L, T, S, RT, MODEL, WALLS>(c);
       return launch_tma_t<L, T, S, RT, MODEL, WALLS>(c);
     }
   }

@@ -15,10 +15,14 @@
 //   raw_full  : the producer's tensor copies of the TX interior columns (+ y-halo rows);
 //   raw_free  : 4 staging + 8 collision warps are done with the raw plane;
 //   fld_full  : 4 local staging warps + 4 staging warps of each x-neighbour have written
-//               their part of the field slot (12 arrivals, release/acquire at cluster scope);
+//               their part of the field slot (12 arrivals; the remote ones release at
+//               cluster scope, the waits acquire at cluster scope);
 //   fld_free  : the 8 local collision warps are done with the field slot;
 //   nbr_free  : the 8 collision warps of each x-neighbour are done with their field slot
 //               (16 arrivals), so that this block may write its edge columns into them.
+//               These arrivals are relaxed: they follow the last use of every value read
+//               from the slot, and a release at cluster scope would make the collision warp
+//               wait for its own outstanding global stores.
 // Staging of plane J waits fld_free(J-4) and nbr_free(J-4); collision of plane J waits
 // fld_full of J-1, J, J+1.  No wait is on an earlier plane's event of the same block than
 // the waiter's own, so the pipeline cannot deadlock; every wait is bounded, a timeout sets
@@ -47,13 +51,11 @@ __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_rel_cluster(uint64_t* bar) {
-  uint64_t state;
-  asm volatile("mbarrier.arrive.release.cluster.shared::cta.b64 %0, [%1];"
-               : "=l"(state)
-               : "r"(smem_addr(bar))
-               : "memory");
-  (void)state;
+// Relaxed remote arrival: no fence.  Used where the arrival only releases shared-memory
+// entries this thread has already read and consumed (a release at cluster scope would
+// also wait for the thread's outstanding global stores).
+__device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
@@ -92,8 +94,12 @@ __host__ __device__ constexpr size_t tmac_smem_bytes() {
 // Launch: cluster dims (C, 1, 1) with C = p.ncx = nx / TX; grid = p.nblk clusters * C
 // blocks; p.ncol = ny / TY tile rows (the work partition's columns); cluster c owns the
 // tile-row-planes [c*U/nblk, (c+1)*U/nblk), U = ncol * nz.
+// Two blocks per SM where the shared memory allows it (one population set).
+template <int MODEL>
+__host__ __device__ constexpr int tmac_min_blocks() { return ModelTraits<MODEL>::K == 1 ? 2 : 1; }
+
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+__global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
     step_kernel_tmac(const __grid_constant__ TmaMaps maps, S* __restrict__ fout, RT* __restrict__ rout,
                      const uint8_t* __restrict__ solid, int* __restrict__ status, StepParams<T> p) {
   static_assert(TX * TY == 32 * kCollideWarps, "one collision thread per tile node");
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         }
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive_rel_cluster(&fld_full[fs]);
+          mbar_arrive(&fld_full[fs]);  // local readers: CTA-scope release
           mbar_arrive_remote(mapa_shared(smem_addr(&fld_full[fs]), left));
           mbar_arrive_remote(mapa_shared(smem_addr(&fld_full[fs]), right));
           mbar_arrive(&raw_free[s]);
@@ -253,8 +259,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     // ---------------- collision ----------------
     const int tx = tid % TX, ty = tid / TX;
     const int e0 = (ty + 1) * EX + (tx + 1);
-    const long long nxl = p.nx;
-    const long long plane_n = (long long)p.nx * p.ny;
+    // 32-bit node indices: the launcher guarantees K * Q * N < 2^31
+    const int nxl = p.nx;
+    const int plane_n = p.nx * p.ny;
+    const int N32 = (int)N;
     const int gx = x0 + tx;
     const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;
     WorkRange work(cid, p.nblk, p.ncol, p.nz);
@@ -268,8 +276,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       if (lane == 0) {
         const int fs = Jf % kFieldSlots;
         mbar_arrive(&fld_free[fs]);
-        mbar_arrive_remote(mapa_shared(smem_addr(&nbr_free[fs]), left));
-        mbar_arrive_remote(mapa_shared(smem_addr(&nbr_free[fs]), right));
+        mbar_arrive_remote_relaxed(mapa_shared(smem_addr(&nbr_free[fs]), left));
+        mbar_arrive_remote_relaxed(mapa_shared(smem_addr(&nbr_free[fs]), right));
       }
     };
     auto release_raw = [&](int Jr) {  // a plane whose raw data this warp does not read
@@ -282,7 +290,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       const int y0 = sg.col * TY;
       const int gy = y0 + ty;
       const int ym = gy == 0 ? p.ny - 1 : gy - 1, yp = gy + 1 >= p.ny ? 0 : gy + 1;
-      const long long rowm = ym * nxl, row0 = gy * nxl, rowp = yp * nxl;
+      const int rowm = ym * nxl, row0 = gy * nxl, rowp = yp * nxl;
       const int np = sg.z1 - sg.z0 + 2;  // planes z0-1 .. z1
       if (!release_raw(J)) {              // leading halo plane: nothing to collide
         ok = false;
@@ -334,17 +342,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
           }
           const int zz = z, zm = zz == 0 ? p.nz - 1 : zz - 1, zpp = zz + 1 >= p.nz ? 0 : zz + 1;
-          const long long pm = zm * plane_n, p0 = zz * plane_n, pp = zpp * plane_n;
-          const long long n0 = gx + row0 + p0;
+          const int pm = zm * plane_n, p0 = zz * plane_n, pp = zpp * plane_n;
+          const int n0 = gx + row0 + p0;
 #pragma unroll
-          for (int k = 0; k < K; k++) rout[(long long)k * N + n0] = RT(cs[k].q);
+          for (int k = 0; k < K; k++) rout[k * N32 + n0] = RT(cs[k].q);
 #pragma unroll
           for (int i = 0; i < Q; i++) {
             const int dxv = cx<L>(i), dyv = cy<L>(i), dzv = cz<L>(i);
-            const long long X = dxv == 0 ? gx : (dxv > 0 ? xp : xm);
-            const long long Y = dyv == 0 ? row0 : (dyv > 0 ? rowp : rowm);
-            const long long Z = dzv == 0 ? p0 : (dzv > 0 ? pp : pm);
-            long long nd = X + Y + Z;
+            const int X = dxv == 0 ? gx : (dxv > 0 ? xp : xm);
+            const int Y = dyv == 0 ? row0 : (dyv > 0 ? rowp : rowm);
+            const int Z = dzv == 0 ? p0 : (dzv > 0 ? pp : pm);
+            int nd = X + Y + Z;
             int id = i;
             const int sl = slot_of(dzv);
             const int ed = e0 + dyv * EX + dxv;
@@ -358,7 +366,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             for (int k = 0; k < K; k++) {
               T val = g[k][i];
               if (i != 0 && !bounce) val += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(sl * NV + NF + k) * NE + ed]);
-              fout[(long long)(k * Q + id) * N + nd] = st_s<S, T>(val);
+              fout[(k * Q + id) * N32 + nd] = st_s<S, T>(val);
             }
           }
         }
