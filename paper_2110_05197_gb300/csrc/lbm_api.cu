@@ -92,7 +92,7 @@ size_t workspace_layout(const lbm_params& p, lbm_ctx* c) {
   const size_t or0 = take((size_t)K * N * relt);
   const size_t or1 = take((size_t)K * N * relt);
   const size_t osol = take((size_t)N);
-  const size_t ostg = take((size_t)5 * N * sizeof(double));
+  const size_t ostg = take((size_t)6 * N * sizeof(double));
   const size_t opar = take((size_t)nblk * LBM_NTOTALS * sizeof(double));
   const size_t odia = take(sizeof(lbm_diag));
   const bool rep = p.model == LBM_MODEL_CG && p.rep_pi != 0.0;

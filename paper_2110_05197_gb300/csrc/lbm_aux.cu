@@ -76,38 +76,43 @@ AuxParams aux_params(const lbm_ctx* c) {
 // tripped blow-up check (the host cannot know when that happened).
 __device__ __forceinline__ int state_index(const lbm_diag* d, int cur) { return d->status ? d->trip_buf : cur; }
 
+// Compute type of the step for a storage type: per-node arithmetic of the auxiliary
+// kernels runs in it (FP64 only for FP64 storage); sums over the lattice stay FP64.
+template <class S>
+using step_t = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+
 // 3 sum_i w_i phi(x + c_i) c_i with a wall neighbour replaced by the centre value.
-template <class L>
-__device__ void grad_fp64(const double* phi, const uint8_t* solid, long long n, int x, int y, int z,
-                          const AuxParams& a, double g[3]) {
-  g[0] = g[1] = g[2] = 0.0;
+template <class L, class C>
+__device__ void grad_c(const double* phi, const uint8_t* solid, long long n, int x, int y, int z,
+                       const AuxParams& a, C g[3]) {
+  g[0] = g[1] = g[2] = C(0);
   for (int q = 0; q < L::NP; q++) {
     const int i = 2 * q + 1;
     const long long mp = nb_index(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
     const long long mm = nb_index(x, y, z, -cx<L>(i), -cy<L>(i), -cz<L>(i), a.nx, a.ny, a.nz);
-    const double vp = (solid && solid[mp]) ? phi[n] : phi[mp];
-    const double vm = (solid && solid[mm]) ? phi[n] : phi[mm];
-    const double d = 3.0 * L::w(L::pgrp(q)) * (vp - vm);
-    g[0] += L::pcx(q) * d;
-    g[1] += L::pcy(q) * d;
-    g[2] += L::pcz(q) * d;
+    const C vp = C((solid && solid[mp]) ? phi[n] : phi[mp]);
+    const C vm = C((solid && solid[mm]) ? phi[n] : phi[mm]);
+    const C d = C(3.0 * L::w(L::pgrp(q))) * (vp - vm);
+    g[0] += C(L::pcx(q)) * d;
+    g[1] += C(L::pcy(q)) * d;
+    g[2] += C(L::pcz(q)) * d;
   }
 }
 
 // Eq. equiliCG for one colour (phi from Eq. phi, enhanced part optional) or Eq. equiliSC
-// (phi = w, no enhanced part), minus phi_i * rref, into out[Q].
-template <class L>
-__device__ void feq_dev(double rho_k, const double* phi, double nubar_en, const double u[3], const double g[3],
-                        double rref, double* out) {
-  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+// (phi = w, no enhanced part), minus phi_i * rref, into out[Q]; drho = rho_k - rref (exact
+// in FP64, then rounded), so every term is a small deviation.
+template <class L, class C>
+__device__ void feq_dev(C rho_k, const double* phi, C nubar_en, const C u[3], const C g[3], C drho, C* out) {
+  const C uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const C ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
   for (int i = 0; i < L::Q; i++) {
     const int gr = grp<L>(i);
-    const double cu = cx<L>(i) * u[0] + cy<L>(i) * u[1] + cz<L>(i) * u[2];
-    const double cgr = cx<L>(i) * g[0] + cy<L>(i) * g[1] + cz<L>(i) * g[2];
-    const double w = L::w(gr);
-    const double enh = nubar_en * (L::psi(gr) * ug + 2.0 * L::xi(gr) * cu * cgr);
-    out[i] = enh + phi[gr] * (rho_k - rref) + rho_k * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    const C cu = C(cx<L>(i)) * u[0] + C(cy<L>(i)) * u[1] + C(cz<L>(i)) * u[2];
+    const C cgr = C(cx<L>(i)) * g[0] + C(cy<L>(i)) * g[1] + C(cz<L>(i)) * g[2];
+    const C w = C(L::w(gr));
+    const C enh = nubar_en * (C(L::psi(gr)) * ug + C(2.0 * L::xi(gr)) * cu * cgr);
+    out[i] = enh + C(phi[gr]) * drho + rho_k * w * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
   }
 }
 
@@ -115,8 +120,9 @@ template <class L, class S, class RT>
 __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __restrict__ ra, RT* __restrict__ rb_,
                                const double* __restrict__ rr, const double* __restrict__ rb,
                                const double* __restrict__ U, const uint8_t* __restrict__ solid, AuxParams a) {
+  using C = step_t<S>;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
-    double out[L::Q];
+    C out[L::Q];
     if (solid && solid[n]) {
       for (int k = 0; k < a.K; k++) {
         ra[(long long)k * a.n + n] = RT(0);
@@ -129,29 +135,29 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
       continue;
     }
     const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
-    double u[3] = {0.0, 0.0, 0.0};
+    C u[3] = {C(0), C(0), C(0)};
     if (U) {
-      u[0] = U[n];
-      u[1] = U[a.n + n];
-      u[2] = U[2 * a.n + n];
+      u[0] = C(U[n]);
+      u[1] = C(U[a.n + n]);
+      u[2] = C(U[2 * a.n + n]);
     }
     for (int k = 0; k < a.K; k++) {
       const double* phi = k == 0 ? rr : rb;
       const RT rref = RT(phi[n]);  // reference density: the initial density, rounded
-      double g[3] = {0.0, 0.0, 0.0};
-      double en = 0.0;
+      C g[3] = {C(0), C(0), C(0)};
+      C en = C(0);
       if (a.model == LBM_MODEL_CG) {
-        grad_fp64<L>(phi, solid, n, x, y, z, a, g);
+        grad_c<L, C>(phi, solid, n, x, y, z, a, g);
         const double r = rr[n], b = rb[n], rho = r + b;
         const double nubar = 1.0 / ((r / rho) / a.nu_r + (b / rho) / a.nu_b);  // Eq. interpVisc
-        en = a.enhanced ? nubar : 0.0;
+        en = a.enhanced ? C(nubar) : C(0);
       }
-      feq_dev<L>(phi[n], a.phi[k], en, u, g, (double)rref, out);
+      feq_dev<L, C>(C(phi[n]), a.phi[k], en, u, g, C(phi[n] - (double)rref), out);
       ra[(long long)k * a.n + n] = rref;
       rb_[(long long)k * a.n + n] = rref;
       for (int i = 0; i < L::Q; i++) {
-        fa[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(out[i]);
-        fb[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(out[i]);
+        fa[(long long)(k * L::Q + i) * a.n + n] = st_s<S, C>(out[i]);
+        fb[(long long)(k * L::Q + i) * a.n + n] = st_s<S, C>(out[i]);
       }
     }
   }
@@ -200,7 +206,8 @@ __global__ void export_kernel(const S* __restrict__ f0, const S* __restrict__ f1
 template <class L, class S, class RT>
 __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__ f1, const RT* __restrict__ r0,
                                  const RT* __restrict__ r1, const lbm_diag* __restrict__ d, int cur,
-                                 double* __restrict__ rr, double* __restrict__ rb, AuxParams a) {
+                                 double* __restrict__ rr, double* __restrict__ rb, double* __restrict__ psi,
+                                 AuxParams a) {
   const int b = state_index(d, cur);
   const S* f = b ? f1 : f0;
   const RT* r = b ? r1 : r0;
@@ -212,6 +219,8 @@ __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__
         s += to_d(r[(long long)k * a.n + m]);  // sum_i phi_i = 1
       }
       (k == 0 ? rr : rb)[m] = s;
+      // Eq. pseudopotential, once per node (the force stencil reads it 18 times)
+      if (k == 0 && a.model == LBM_MODEL_SC_MP) psi[m] = a.rho0 * (1.0 - exp(-s / a.rho0));
     }
   }
 }
@@ -253,20 +262,18 @@ __device__ void block_reduce(Acc& a) {
   }
 }
 
-// compute type of the step for a storage type (the repulsion pre-pass fields use it)
-template <class S>
-using step_t = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
-
 template <class L, class S, class RT>
 __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict__ f0, const S* __restrict__ f1,
                                                             const RT* __restrict__ r0, const RT* __restrict__ r1,
                                                             const lbm_diag* __restrict__ d, int cur,
                                                             const double* __restrict__ rr,
                                                             const double* __restrict__ rb,
+                                                            const double* __restrict__ psi,
                                                             const uint8_t* __restrict__ solid, double* __restrict__ uo,
                                                             double* __restrict__ partials, AuxParams a,
                                                             const step_t<S>* __restrict__ colour,
                                                             const step_t<S>* __restrict__ normals, RepParams rp) {
+  using C = step_t<S>;  // per-node arithmetic; the sums below are FP64
   const int bsel = state_index(d, cur);
   const S* f = bsel ? f1 : f0;
   const RT* rref = bsel ? r1 : r0;
@@ -274,50 +281,58 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
   acc_init(acc);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
     const bool wall = solid && solid[n];
+    // momentum in FP64: the colours' momenta nearly cancel at interfaces, so summing the
+    // stored values in the compute precision would add its rounding to the reported u
     double j[3] = {0.0, 0.0, 0.0};
     int bad = 0;
     for (int k = 0; k < a.K; k++) {
-      const double rk = to_d(rref[(long long)k * a.n + n]);
+      const C rk = C(rref[(long long)k * a.n + n]);
       if (!isfinite(rk)) bad = 1;
-      for (int i = 0; i < L::Q; i++) {
-        // the shift phi_i r is symmetric in c_i and carries no momentum
-        const double v = to_d(f[(long long)(k * L::Q + i) * a.n + n]);
-        if (!isfinite(v)) bad = 1;
-        j[0] += cx<L>(i) * v;
-        j[1] += cy<L>(i) * v;
-        j[2] += cz<L>(i) * v;
+      // the shift phi_i r is symmetric in c_i and carries no momentum: opposite-pair
+      // differences of the stored deviations
+#pragma unroll
+      for (int q = 0; q < L::NP; q++) {
+        const double vp = to_d(f[(long long)(k * L::Q + 2 * q + 1) * a.n + n]);
+        const double vm = to_d(f[(long long)(k * L::Q + 2 * q + 2) * a.n + n]);
+        if (!isfinite(vp) || !isfinite(vm)) bad = 1;
+        const double dv = vp - vm;
+        if (L::pcx(q)) j[0] += L::pcx(q) * dv;
+        if (L::pcy(q)) j[1] += L::pcy(q) * dv;
+        if (L::pcz(q)) j[2] += L::pcz(q) * dv;
       }
+      if (!isfinite(to_d(f[(long long)(k * L::Q) * a.n + n]))) bad = 1;
     }
     const double r = rr[n], b = rb[n], rho = r + b;
     double F[3] = {a.body[0], a.body[1], a.body[2]};
     if (!wall && a.model == LBM_MODEL_CG && normals) {
       const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
-      step_t<S> Fr[3];
-      rep_force<L, step_t<S>>(normals, colour, solid, x, y, z, rp, Fr);
-      for (int dd = 0; dd < 3; dd++) F[dd] += (double)Fr[dd];
+      C Fr[3];
+      rep_force<L, C>(normals, colour, solid, x, y, z, rp, Fr);  // the step's own precision
+      for (int dd = 0; dd < 3; dd++) F[dd] += double(Fr[dd]);
     }
     if (!wall && a.model != LBM_MODEL_CG) {
       const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+      // sum_i w_i phi(x + c_i) c_i as opposite-pair differences in FP64 (the force is a
+      // small difference of O(1) values)
       double s1[3] = {0.0, 0.0, 0.0}, s2[3] = {0.0, 0.0, 0.0};
-      const double psic = a.rho0 * (1.0 - exp(-r / a.rho0));
-      for (int i = 1; i < L::Q; i++) {
-        const long long m = nb_index(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
-        const bool sw = solid && solid[m];
-        const double w = L::w(grp<L>(i));
+      const double psic = a.model == LBM_MODEL_SC_MP ? psi[n] : 0.0;
+#pragma unroll
+      for (int q = 0; q < L::NP; q++) {
+        const int i = 2 * q + 1;
+        const long long mp = nb_index(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
+        const long long mm = nb_index(x, y, z, -cx<L>(i), -cy<L>(i), -cz<L>(i), a.nx, a.ny, a.nz);
+        const bool swp = solid && solid[mp], swm = solid && solid[mm];
+        const double w = L::w(L::pgrp(q));
+        double d1, d2 = 0.0;
         if (a.model == LBM_MODEL_SC_MP) {
-          const double ps = sw ? psic : a.rho0 * (1.0 - exp(-rr[m] / a.rho0));
-          s1[0] += w * ps * cx<L>(i);
-          s1[1] += w * ps * cy<L>(i);
-          s1[2] += w * ps * cz<L>(i);
+          d1 = w * ((swp ? psic : psi[mp]) - (swm ? psic : psi[mm]));
         } else {
-          const double v2 = sw ? b : rb[m], v1 = sw ? r : rr[m];
-          s1[0] += w * v2 * cx<L>(i);
-          s1[1] += w * v2 * cy<L>(i);
-          s1[2] += w * v2 * cz<L>(i);
-          s2[0] += w * v1 * cx<L>(i);
-          s2[1] += w * v1 * cy<L>(i);
-          s2[2] += w * v1 * cz<L>(i);
+          d1 = w * ((swp ? b : rb[mp]) - (swm ? b : rb[mm]));
+          d2 = w * ((swp ? r : rr[mp]) - (swm ? r : rr[mm]));
         }
+        if (L::pcx(q)) { s1[0] += L::pcx(q) * d1; s2[0] += L::pcx(q) * d2; }
+        if (L::pcy(q)) { s1[1] += L::pcy(q) * d1; s2[1] += L::pcy(q) * d2; }
+        if (L::pcz(q)) { s1[2] += L::pcz(q) * d1; s2[2] += L::pcz(q) * d2; }
       }
       for (int dd = 0; dd < 3; dd++) {
         if (a.model == LBM_MODEL_SC_MP)
@@ -327,8 +342,10 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
       }
     }
     double u[3] = {0.0, 0.0, 0.0};
-    if (!wall)
-      for (int dd = 0; dd < 3; dd++) u[dd] = (j[dd] + 0.5 * F[dd]) / rho;
+    if (!wall) {
+      const double inv = 1.0 / rho;
+      for (int dd = 0; dd < 3; dd++) u[dd] = (j[dd] + 0.5 * F[dd]) * inv;
+    }
     if (uo) {
       uo[n] = u[0];
       uo[a.n + n] = u[1];
@@ -418,8 +435,9 @@ cudaError_t diag_t(lbm_ctx* c, double* uo) {
   const RT* r1 = static_cast<const RT*>(c->r[1]);
   double* rr = c->stage;
   double* rb = c->stage + c->N;
+  double* psi = c->stage + 5 * c->N;
   densities_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(f0, f1, r0, r1, c->diag, c->cur, rr,
-                                                                               rb, a);
+                                                                               rb, psi, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (c->rep) {
@@ -427,7 +445,7 @@ cudaError_t diag_t(lbm_ctx* c, double* uo) {
     if (e != cudaSuccess) return e;
   }
   diag_kernel<L, S, RT><<<c->nblk_diag, kDiagThreads, 0, c->stream>>>(
-      f0, f1, r0, r1, c->diag, c->cur, rr, rb, c->has_walls ? c->solid : nullptr, uo, c->partials, a,
+      f0, f1, r0, r1, c->diag, c->cur, rr, rb, psi, c->has_walls ? c->solid : nullptr, uo, c->partials, a,
       static_cast<const step_t<S>*>(c->colour), static_cast<const step_t<S>*>(c->normals), rep_params(c));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -33,7 +33,7 @@ struct lbm_ctx {
   int cur;               // index of the buffer pair holding the current state
   uint8_t* solid;        // [N] wall mask (all zero without walls)
   bool has_walls;
-  double* stage;         // [5][N] FP64 staging: rho_r, rho_b, u_x, u_y, u_z
+  double* stage;         // [6][N] FP64 staging: rho_r, rho_b, u_x, u_y, u_z, psi (SC multiphase)
   double* partials;      // [nblk_diag][LBM_NTOTALS]
   int nblk_diag;
   lbm_diag* diag;        // device
@@ -109,8 +109,10 @@ StepParams<T> make_step_params(const lbm_ctx* c) {
   s.nz = q.nz;
   s.ncx = (q.nx + c->tx - 1) / c->tx;
   s.ncol = s.ncx * ((q.ny + c->ty - 1) / c->ty);
-  // chunked grid (tz > 0); a persistent grid's size is set by the launcher
-  s.nblk = c->tz > 0 ? s.ncol * ((q.nz + c->tz - 1) / c->tz) : s.ncol;
+  // chunked grid (tz > 0): one block per unit; a persistent grid (tz = 0) is sized by the
+  // launcher (persistent_plan)
+  s.nchunks = c->tz > 0 ? (q.nz + c->tz - 1) / c->tz : 1;
+  s.nblk = s.ncol * s.nchunks;
   s.n = c->N;
   double phi[2][3];
   rest_weights(q, phi);

@@ -61,11 +61,28 @@ cudaError_t launch_rep_prepass_t(lbm_ctx* c, int buf) {
   return cudaGetLastError();
 }
 
-// Persistent grid: as many blocks as can be resident, at most one per tile-plane.
+// Persistent grid: `resident` blocks (or clusters) loop over the units.  The z-chunk count
+// trades the halo planes every unit re-reads (2 per unit) against the idle share of the
+// last round of units; chunks stay at least 8 planes long.
 template <class T>
-int persistent_blocks(const StepParams<T>& sp, int resident) {
-  const long long U = (long long)sp.ncol * sp.nz;
-  return (int)std::max<long long>(1, std::min<long long>(U, resident));
+void persistent_plan(StepParams<T>& sp, int resident) {
+  resident = std::max(resident, 1);
+  const int max_chunks = std::max(1, sp.nz / 8);
+  double best = -1.0;
+  int best_n = 1;
+  for (int n = 1; n <= max_chunks; n++) {
+    const long long units = (long long)sp.ncol * n;
+    const long long rounds = (units + resident - 1) / resident;
+    const double busy = double(units) / double(rounds * resident);  // share of block-rounds with a unit
+    const double planes = double(sp.nz) / n;
+    const double score = busy / (1.0 + 1.0 / planes);  // halo planes cost about half a plane each
+    if (score > best + 1e-9) {
+      best = score;
+      best_n = n;
+    }
+  }
+  sp.nchunks = best_n;
+  sp.nblk = (int)std::min<long long>((long long)sp.ncol * best_n, resident);
 }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS>
@@ -81,7 +98,7 @@ cudaError_t launch_tma_t(lbm_ctx* c) {
   }
   dim3 block(kTmaThreads, 1, 1);
   StepParams<T> sp = make_step_params<T>(c);
-  if (c->tz == 0) sp.nblk = persistent_blocks(sp, c->nsm);  // one block per SM (shared memory)
+  if (c->tz == 0) persistent_plan(sp, c->nsm);  // one block per SM (shared memory)
   dim3 grid(sp.nblk, 1, 1);
   const S* fin = static_cast<const S*>(c->f[c->cur]);
   const RT* rin = static_cast<const RT*>(c->r[c->cur]);
@@ -120,7 +137,7 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (c->tz > 0) {
-    sp.nblk = sp.ncol * ((c->p.nz + c->tz - 1) / c->tz);
+    sp.nblk = sp.ncol * sp.nchunks;
   } else {
     const void* fn = reinterpret_cast<const void*>(kern);
     if (c->occ_fn != fn || c->occ_tx != -C) {
@@ -133,7 +150,7 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
       c->occ_ty = 0;
       c->occ_blocks = ncl > 0 ? ncl : 1;
     }
-    sp.nblk = persistent_blocks(sp, c->occ_blocks);  // clusters
+    persistent_plan(sp, c->occ_blocks);  // clusters
   }
   cfg.gridDim = dim3(sp.nblk * C, 1, 1);
   S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
@@ -177,7 +194,7 @@ cudaError_t launch_step_t(lbm_ctx* c) {
       c->occ_ty = ty;
       c->occ_blocks = nb > 0 ? nb : 1;
     }
-    sp.nblk = persistent_blocks(sp, c->nsm * c->occ_blocks);
+    persistent_plan(sp, c->nsm * c->occ_blocks);
   }
   dim3 grid(sp.nblk, 1, 1);
   const S* fin = static_cast<const S*>(c->f[c->cur]);

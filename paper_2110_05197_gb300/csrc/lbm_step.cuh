@@ -49,7 +49,8 @@ template <class T>
 struct StepParams {
   int nx, ny, nz;
   int ncx, ncol;          // block columns along x, and in total (ncx * columns along y)
-  int nblk;               // blocks in the grid: block b owns tile-planes [b*U/nblk, (b+1)*U/nblk)
+  int nchunks;            // z-chunks per column
+  int nblk;               // blocks in the grid (WorkRange)
   long long n;            // nodes
   T phi[2][3];            // rest-state weights per component and group (CG: Eq. phi; SC: w)
   // CG
@@ -120,30 +121,27 @@ __device__ __forceinline__ T two_sum(T a, T b, T& e) {
 }
 
 // Work partition.  The lattice is cut into ncol block columns (tiles of TX x TY nodes,
-// all of z); a tile-plane is one tile at one z, numbered col * nz + z, U = ncol * nz in
-// all.  Block b owns the contiguous range [b*U/nblk, (b+1)*U/nblk): with nblk = ncol *
-// ceil(nz/tz) every range is one balanced z-chunk of one column; with nblk = the resident
-// block count (a persistent grid) every block gets the same number of tile-planes, split
-// into runs (segments) of consecutive z in one column, each marched with its own halo
-// planes.
+// all of z) and every column's nz planes into nchunks z-chunks of near-equal length; a
+// work unit is one (chunk, column) pair, numbered u = chunk * ncol + col.  Block b takes the
+// units b, b + nblk, b + 2 nblk, ...: with nblk = ncol * nchunks (one unit per block) the
+// hardware runs them in waves, with nblk = the resident block count (a persistent grid)
+// every block loops.  Either way the blocks running at one time hold consecutive units,
+// i.e. neighbouring columns at the same z, so the halo rows one block reads were just
+// read (and are still in L2) for its neighbour.  A unit is marched with its own halo planes.
 struct Segment {
   int col, z0, z1;  // column and z range [z0, z1)
 };
 struct WorkRange {
-  long long next, end;
-  __device__ WorkRange(int b, int nblk, int ncol, int nz) {
-    const long long U = (long long)ncol * nz;
-    next = (long long)b * U / nblk;
-    end = (long long)(b + 1) * U / nblk;
-  }
-  __device__ bool pop(int nz, Segment& s) {
+  int next, end, stride, ncol, nz, nchunks;
+  __device__ WorkRange(int b, int nblk, int ncol_, int nz_, int nchunks_)
+      : next(b), end(ncol_ * nchunks_), stride(nblk), ncol(ncol_), nz(nz_), nchunks(nchunks_) {}
+  __device__ bool pop(Segment& s) {
     if (next >= end) return false;
-    s.col = (int)(next / nz);
-    s.z0 = (int)(next - (long long)s.col * nz);
-    const long long col_end = (long long)(s.col + 1) * nz;
-    const long long e = end < col_end ? end : col_end;
-    s.z1 = s.z0 + (int)(e - next);
-    next = e;
+    const int chunk = next / ncol;
+    s.col = next - chunk * ncol;
+    s.z0 = (int)(((long long)chunk * nz) / nchunks);
+    s.z1 = (int)(((long long)(chunk + 1) * nz) / nchunks);
+    next += stride;
     return true;
   }
 };
@@ -592,9 +590,9 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
     }
   };
 
-  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
   Segment sg;
-  while (work.pop(p.nz, sg)) {
+  while (work.pop(sg)) {
     x0 = (sg.col % p.ncx) * TX;
     y0 = (sg.col / p.ncx) * TY;
     gx = x0 + tx;

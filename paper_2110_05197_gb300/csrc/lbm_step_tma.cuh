@@ -247,12 +247,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   if (warp == kCollideWarps + kStageWarps) {
     // ---------------- producer ----------------
     if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.pop_main_mid) : "memory");
-    WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+    WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
     Segment sg;
     int J = 0;
     bool ok = true;
     const long long plane_n = (long long)p.nx * p.ny;
-    while (ok && work.pop(p.nz, sg)) {
+    while (ok && work.pop(sg)) {
       const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
       const int yt = y0 == 0 ? p.ny - 1 : y0 - 1, yb = y0 + TY == p.ny ? 0 : y0 + TY;
       // x of the 4-byte halo words: the word holding x0-1 (periodic) and the one at x0+TX;
@@ -308,10 +308,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   if (warp >= kCollideWarps) {
     // ---------------- staging ----------------
     const int stid = tid - 32 * kCollideWarps;
-    WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+    WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
     Segment sg;
     int J = 0;
-    while (work.pop(p.nz, sg)) {
+    while (work.pop(sg)) {
       const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
       for (int z = sg.z0 - 1; z <= sg.z1; z++, J++) {
         const int s = J % kRawSlots, fs = J % kFieldSlots;
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   const int e0 = (ty + 1) * EX + (tx + 1);
   const long long nxl = p.nx;
   const long long plane_n = (long long)p.nx * p.ny;
-  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz);
+  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
   Segment sg;
   int J = 0;  // global index of the segment's first (halo) plane
   auto release_raw = [&](int Jr) {  // a plane whose raw data this warp does not read
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     if (lane == 0) mbar_arrive(&raw_free[Jr % kRawSlots]);
     return true;
   };
-  while (work.pop(p.nz, sg)) {
+  while (work.pop(sg)) {
     const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
     const int gx = x0 + tx, gy = y0 + ty;
     const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;

@@ -158,11 +158,11 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
     // ---------------- producer ----------------
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(&maps.pop_main_mid) : "memory");
-      WorkRange work(cid, p.nblk, p.ncol, p.nz);
+      WorkRange work(cid, p.nblk, p.ncol, p.nz, p.nchunks);
       Segment sg;
       int J = 0;
       bool ok = true;
-      while (ok && work.pop(p.nz, sg)) {
+      while (ok && work.pop(sg)) {
         const int y0 = sg.col * TY;
         const int yt = y0 == 0 ? p.ny - 1 : y0 - 1, yb = y0 + TY == p.ny ? 0 : y0 + TY;
         for (int z = sg.z0 - 1; z <= sg.z1; z++, J++) {
@@ -194,11 +194,11 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
   } else if (warp >= kCollideWarps) {
     // ---------------- staging ----------------
     const int stid = tid - 32 * kCollideWarps;
-    WorkRange work(cid, p.nblk, p.ncol, p.nz);
+    WorkRange work(cid, p.nblk, p.ncol, p.nz, p.nchunks);
     Segment sg;
     int J = 0;
     bool ok = true;
-    while (ok && work.pop(p.nz, sg)) {
+    while (ok && work.pop(sg)) {
       const int y0 = sg.col * TY;
       for (int z = sg.z0 - 1; z <= sg.z1; z++, J++) {
         const int s = J % kRawSlots, fs = J % kFieldSlots;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
     const int N32 = (int)N;
     const int gx = x0 + tx;
     const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;
-    WorkRange work(cid, p.nblk, p.ncol, p.nz);
+    WorkRange work(cid, p.nblk, p.ncol, p.nz, p.nchunks);
     Segment sg;
     int J = 0;  // global index of the segment's first (halo) plane
     bool ok = true;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
       if (lane == 0) mbar_arrive(&raw_free[Jr % kRawSlots]);
       return true;
     };
-    while (ok && work.pop(p.nz, sg)) {
+    while (ok && work.pop(sg)) {
       const int y0 = sg.col * TY;
       const int gy = y0 + ty;
       const int ym = gy == 0 ? p.ny - 1 : gy - 1, yp = gy + 1 >= p.ny ? 0 : gy + 1;

@@ -57,7 +57,8 @@ def test_workspace_size_query(L):
     N = 128 ** 3
     pops = 2 * 2 * 19 * N * 4   # A/B populations
     ref = 2 * 2 * N * 4         # A/B reference densities
-    assert pops + ref < b < pops + ref + 5 * N * 8 + 2 * N + (1 << 20)
+    # + FP64 staging for moments (rho_r, rho_b, u, psi: 6 N doubles), wall mask, partials
+    assert pops + ref < b < pops + ref + 6 * N * 8 + 2 * N + (1 << 20)
     rc, b64 = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP64, model=lbm.CG)
     assert b64 - b == 2 * 2 * 19 * N * 4 + ref
     rc, b16 = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP16, model=lbm.CG)
