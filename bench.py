@@ -55,6 +55,34 @@ def sc_kw(n=N3, nz=None):
     return dict(lattice=1, model=1, nx=n, ny=n, nz=nz or n, G=-5.0, rho0_psi=1.0, tau_r=1.0)
 
 
+def csrc_sha256_16():
+    """Hash of the CUDA sources (the kernels whose counters a profile records)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2110_05197_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary under profiles/,
+    or None when no summary exists or the kernel sources changed since it was taken."""
+    import glob
+    sha = csrc_sha256_16()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as f:
+            for line in f:
+                if not line.startswith("roofline-traffic:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if kv.get("kernel") == kernel and kv.get("csrc_sha256_16") == sha:
+                    return int(kv["bytes_per_launch"])
+    return None
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -144,8 +172,10 @@ def dist_env():
     return ws, rank, local
 
 
-def oracle_sample_mlups(steps: int, nz: int = 16, threads: int | None = None):
-    """FP64 CPU oracle on a 128 x 128 x nz slab of the same droplet workload (CG + SC)."""
+def oracle_sample_mlups(steps: int, nz: int = 16, threads: int | None = None, budget_s: float | None = None):
+    """FP64 CPU oracle on a 128 x 128 x nz slab of the same droplet workload (CG + SC).
+    With budget_s, steps is the minimum and the loop runs on until budget_s seconds
+    (bounded CPU work); returns (MLUPS, threads, seconds, nodes per lattice, steps)."""
     import oracle
     oracle.build()
     threads = threads or os.cpu_count() or 1
@@ -155,20 +185,22 @@ def oracle_sample_mlups(steps: int, nz: int = 16, threads: int | None = None):
     sc = oracle.OracleSim(oracle.Params(**sc_kw(N3, nz))).init(rho)
     n = N3 * N3 * nz
     t0 = time.perf_counter()
-    for _ in range(steps):
+    done = 0
+    while done < steps or (budget_s is not None and time.perf_counter() - t0 < budget_s):
         cg.step(1)
         sc.step(1)
+        done += 1
     dt = time.perf_counter() - t0
-    return 2 * n * steps / dt / 1e6, oracle.get_threads(), dt, n
+    return 2 * n * done / dt / 1e6, oracle.get_threads(), dt, n, done
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    nz = 8
-    mlups_w, cores, _, n = oracle_sample_mlups(max(1, args.warmup), nz)
-    mlups, cores, dt, n = oracle_sample_mlups(args.steps, nz)
+    nz = 32
+    oracle_sample_mlups(max(1, args.warmup), nz)
+    mlups, cores, dt, n, _ = oracle_sample_mlups(args.steps, nz)
     sample = f"128x128x{nz} slab of the 128^3 droplet workload, CG + SC FP64 oracle, {args.steps} steps"
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -261,6 +293,9 @@ def run_ours(args):
     cg_avg, sc_avg = float(np.mean(cg_ms)), float(np.mean(sc_ms))
     value = 2 * n * K * ws / (total_ms / 1e3) / 1e6
     peak, peak_kind = hbm_peak()
+    # 32 x 8 tiles run the cluster TMA kernel on this 128^3 lattice (nx / 32 = 4 <= 8)
+    cg_kernel = ("step_kernel_tmac<D3Q19,float,CG>" if list(tiling["cg"][:2]) == [32, 8]
+                 else "step_kernel<D3Q19,float,CG>")
     achieved = BYTES_PER_LU["cg"] * n / (cg_avg / 1e3) / 1e9
     tot_cg, rc_cg = cg.totals()
     tot_sc, rc_sc = sc.totals()
@@ -301,7 +336,8 @@ def run_ours(args):
             "cg_mlups": n / (cg_avg / 1e3) / 1e6, "sc_mlups": n / (sc_avg / 1e3) / 1e6,
             "cg_step_ms": cg_avg, "sc_step_ms": sc_avg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "step_kernel<D3Q19,float,CG>",
+                         "frac": achieved / peak, "traffic": profiled_traffic(cg_kernel),
+                         "kernel": cg_kernel,
                          "bytes_per_lu": BYTES_PER_LU["cg"], "peak_kind": peak_kind,
                          "sc": {"achieved": BYTES_PER_LU["sc"] * n / (sc_avg / 1e3) / 1e9,
                                 "frac": BYTES_PER_LU["sc"] * n / (sc_avg / 1e3) / 1e9 / peak}},
@@ -314,9 +350,9 @@ def run_ours(args):
                        "cg_mass_r": tot_cg["mass_r"], "sc_mass": tot_sc["mass_r"]},
         }
         if not args.no_cpu_baseline:
-            mlups_cpu, cores, dt, ns = oracle_sample_mlups(2, 16)
+            mlups_cpu, cores, dt, ns, done = oracle_sample_mlups(1, N3, budget_s=10.0)
             line["cpu_baseline"] = {"value": mlups_cpu, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                                    "sample": f"FP64 oracle, 2 CG + 2 SC steps on a 128x128x16 slab of the "
+                                    "sample": f"FP64 oracle, {done} CG + {done} SC steps of the full 128^3 "
                                               f"workload ({dt:.1f} s)"}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -146,15 +146,16 @@ lbm_status lbm_destroy(lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);
 
 /* Tiling of the fused step kernel: a block owns tiles of tx * ty node columns (tx * ty <=
- * 256 and a multiple of 32) and marches them through z.  tz > 0: the nz planes of each
- * column are split into ceil(nz / tz) chunks of near-equal length, one block per chunk
- * (tz must be 1 for D2Q9).  tz = 0: a persistent grid of as many blocks as fit on the
- * device, each taking an equal share of all tile-planes in column-major order (a share may
- * span two columns).  Default 32 x 8 x 16.
+ * 256 and a multiple of 32) and marches them through z in z-chunks; work units are
+ * (z-chunk, column) pairs taken chunk-major.  tz > 0: ceil(nz / tz) chunks of near-equal
+ * length, one block per unit (tz must be 1 for D2Q9).  tz = 0: a persistent grid of as many
+ * blocks as fit on the device looping over the units, with a chunk count chosen from that
+ * block count.  Default 32 x 8 x 16.
  * D3Q19 lattices in FP32/FP16/BF16 with nx % 32 == 0 and ny % 8 == 0 run the TMA-staged
- * kernel when tx x ty is 32 x 8, the generic kernel otherwise.  Results are bitwise
- * independent of the shape within each kernel; the two kernels agree to a few ulps of the
- * stored populations (the compiler fuses multiply-adds differently).  LBM_EINVAL for
+ * kernel when tx x ty is 32 x 8 (for nx <= 256 as clusters of nx / 32 blocks that exchange
+ * the x-halo in distributed shared memory), the generic kernel otherwise.  Results are
+ * bitwise independent of the shape within each kernel; the kernels agree to a few ulps of
+ * the stored populations (the compiler fuses multiply-adds differently).  LBM_EINVAL for
  * shapes outside those limits. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t tx, int32_t ty, int32_t tz);
 

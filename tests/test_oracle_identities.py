@@ -51,14 +51,28 @@ def test_velocity_set_and_weights(orc, lat):
         assert sum(W[i] * int(c[i, a]) for i in range(Q)) == 0
 
 
+def _golden_constants():
+    """tests/golden/d3q19_printed_constants.txt: the D3Q19 w, B, psi, xi values printed in
+    Sec. 2.2 (Eqs. weights, perturbationOp, equiliCG)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "d3q19_printed_constants.txt")
+    want = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        name, grp, val = line.split()
+        want.setdefault(name, {})[int(grp)] = Fraction(val)
+    return want
+
+
 def test_d3q19_printed_values(orc):
-    """Eq. weights and the B_i, psi_i, xi_i values printed with Eqs. perturbationOp, phi."""
+    """The oracle's D3Q19 tables equal the values printed with Eqs. weights,
+    perturbationOp and equiliCG (golden fixture)."""
     c, w, B, psi, xi = orc.lattice_tables(1)
     grp = [0] + [1] * 6 + [2] * 12
-    want = {"w": (Fraction(1, 3), Fraction(1, 18), Fraction(1, 36)),
-            "B": (Fraction(-2, 9), Fraction(1, 54), Fraction(1, 27)),
-            "psi": (Fraction(-5, 2), Fraction(-1, 6), Fraction(1, 24)),
-            "xi": (Fraction(0), Fraction(1, 4), Fraction(1, 8))}
+    want = _golden_constants()
+    assert set(want) == {"w", "B", "psi", "xi"}
     for name, arr in (("w", w), ("B", B), ("psi", psi), ("xi", xi)):
         for i in range(19):
             assert _frac(arr[i]) == want[name][grp[i]], (name, i)

@@ -352,3 +352,64 @@ def test_repulsion_in_thin_film(orc):
     assert F[20] > 1e-4 and abs(F[20] + F[21]) < 1e-15
     Fall = s.force()
     assert np.max(np.abs(Fall[1:])) == 0.0
+
+
+@pytest.mark.slow
+def test_droplet_oscillation_miller_scriven(orc):
+    """Sec. 3.2: an ellipsoidal CG droplet (ratio 1, tau = 0.52, A = 0.02, semi-axes
+    8.8 / 7.63 / 7.63 in a 28^3 box) oscillates in its second mode at the frequency of
+    Eqs. millscriv, millscriv2, millscriv3.  R(t) is the radius along y through the centre
+    (rho^N = 0, linearly interpolated), fitted with R_D + a exp(-b t) sin(d t + c); the
+    formula takes the run's own R_D and its measured surface tension sigma = dP R_D / 2
+    (dP from the CG pressure p = sum_k rho_k (1 - alpha_k)/2 inside and outside, Eq.
+    CGpressure), rho_in = rho_out = 1 and nu = (tau - 1/2)/3.  The paper reports 11.5% at
+    R_D = 11.65 (Table dropOsc); at R_D ~ 7.6 the bound is 15%, and the oscillation must
+    decay.  A wrong inertia, viscosity or pressure law moves the frequency by far more."""
+    from scipy.optimize import curve_fit
+    n, tau, A, a = 28, 0.52, 0.02, 8.8
+    b = np.sqrt(512.0 / a)
+    c = n // 2
+    x, y, z = inputs.grid(n, n, n)
+    ins = ((x - c) / a) ** 2 + ((y - c) / b) ** 2 + ((z - c) / b) ** 2 <= 1.0
+    rr, rb = inputs.two_fluid(ins, 1.0, 1.0, 0.0, 1)
+    s = _sim(orc, lattice=orc.D3Q19, model=orc.CG, nx=n, ny=n, nz=n, rho_r0=1.0, rho_b0=1.0, tau_r=tau,
+             tau_b=tau, A=A)
+    s.init(rr, rb)
+
+    def radius():
+        r, bl, _, _ = s.moments()
+        rn = ((r - bl) / (r + bl)).reshape(n, n, n)[c, :, c]  # along y at x = z = centre
+        out = []
+        for sgn in (1, -1):
+            for k in range(c - 1):
+                y0, y1 = c + sgn * k, c + sgn * (k + 1)
+                if rn[y0] > 0 >= rn[y1]:
+                    out.append(k + rn[y0] / (rn[y0] - rn[y1]))
+                    break
+        assert len(out) == 2
+        return np.mean(out)
+
+    ts, rs = [], []
+    for t in range(0, 1500, 5):
+        ts.append(t)
+        rs.append(radius())
+        s.step(5)
+    ts, rs = np.array(ts, dtype=float), np.array(rs)
+    r, bl, _, tot = s.moments()
+    rho = (r + bl).reshape(n, n, n)
+    dP = 0.4 * (rho[c, c, c] - rho[0, 0, 0])          # alpha_R = alpha_B = 0.2
+    RD = rs[-40:].mean()
+    sigma = dP * RD / 2
+    nu = (tau - 0.5) / 3
+    w_star = np.sqrt(24 * sigma / (RD ** 3 * (2 + 3)))                               # Eq. millscriv2
+    alpha = 25 * nu / (np.sqrt(2) * RD * (2 + 3) * (2 * np.sqrt(nu)))               # Eq. millscriv3
+    w2 = w_star - 0.5 * alpha * np.sqrt(w_star) + 0.25 * alpha ** 2                 # Eq. millscriv
+    fit = lambda t, R, amp, damp, d, ph: R + amp * np.exp(-damp * t) * np.sin(d * t + ph)
+    sel = ts >= 40
+    p, _ = curve_fit(fit, ts[sel], rs[sel], p0=[RD, -0.5, 1e-3, w2, 0.0], maxfev=20000)
+    err = (p[3] - w2) / w2
+    print(f"Miller-Scriven: R_D {RD:.3f}, sigma {sigma:.5f} (theory {4 / 9 * A * tau:.5f}), "
+          f"omega_2 fit {p[3]:.5f} vs formula {w2:.5f} ({err:+.3f}), damping {p[2]:.2e}")
+    assert abs(err) < 0.15
+    assert p[2] > 0
+    assert 0.8 < sigma / (4 / 9 * A * tau) < 1.1   # sigma = (4/9) A / omega_eff within the Laplace error
