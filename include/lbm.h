@@ -159,6 +159,41 @@ const char* lbm_status_string(lbm_status s);
  * shapes outside those limits. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t tx, int32_t ty, int32_t tz);
 
+/* ---- Batched stepping -------------------------------------------------------------
+ * Many lattices (each an lbm_ctx) advance together: one persistent kernel launch per step
+ * walks a device job table of all their work units (32 x 8 node columns times z-chunks
+ * of <= 16 planes), so small lattices do not pay one launch each and fill the GPU
+ * together.  The per-node arithmetic is the generic step kernel's, so a lattice's result
+ * is bitwise the same alone or in any mix (it may differ by a few ulps from a lattice
+ * stepped with lbm_step_* on the TMA-staged kernel).  Jobs must be initialised, periodic
+ * (no walls), without the repulsion force, of the batch's storage precision and on the
+ * batch's stream.  The periodic diagnostics (diag_every) do not run inside a batch; call
+ * lbm_moments per job.
+ *
+ * lbm_batch_create: precision LBM_FP32, LBM_FP16 or LBM_BF16; capacity max_jobs lattices
+ * and max_units work units.  ws == NULL: *ws_bytes receives the device workspace size
+ * (caller-owned, 256-byte aligned, kept until lbm_batch_destroy).  LBM_EINVAL for another
+ * precision or a non-positive capacity.
+ * lbm_batch_units: work units a lattice occupies (for capacity and admission planning).
+ * lbm_batch_set: the job list; job j takes nsteps[j] further steps over later
+ * lbm_batch_step calls.  Uploads the table on the stream.  LBM_EINVAL when a job does not
+ * fit the rules above or the capacity is exceeded, LBM_ESTATE for an uninitialised or
+ * failed context.
+ * lbm_batch_step: advances every job by min(nsteps, its remaining steps); use_graph != 0
+ * replays the nsteps launches as one CUDA graph (built on the first call with that nsteps,
+ * then reused; the table address is fixed, so lbm_batch_set does not invalidate it).
+ * Asynchronous on the stream; updates each context's step count and current buffer.
+ * lbm_batch_launch_count: step-kernel launches enqueued so far (graph nodes included).
+ * lbm_batch_destroy: NULL-safe; does not touch the jobs or the workspace. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(int32_t precision, int32_t max_jobs, int32_t max_units, void* ws, size_t* ws_bytes,
+                            void* stream, lbm_batch** out);
+lbm_status lbm_batch_units(const lbm_ctx* ctx, int32_t* units);
+lbm_status lbm_batch_set(lbm_batch* batch, lbm_ctx* const* jobs, const int32_t* nsteps, int32_t njobs);
+lbm_status lbm_batch_step(lbm_batch* batch, int32_t nsteps, int32_t use_graph);
+uint64_t lbm_batch_launch_count(const lbm_batch* batch);
+lbm_status lbm_batch_destroy(lbm_batch* batch);
+
 /* Number of kernel launches this context has enqueued since creation (for accounting). */
 uint64_t lbm_launch_count(const lbm_ctx* ctx);
 

@@ -464,27 +464,43 @@ __host__ size_t step_smem_bytes(int tx, int ty) {
 template <class T>
 __host__ __device__ constexpr int min_blocks() { return sizeof(T) == 8 ? 1 : 2; }
 
+// Population and reference arrays of one step: the state at t (in) and at t+1 (out).
+template <class S, class RT>
+struct StepArrays {
+  const S* __restrict__ fin;
+  S* __restrict__ fout;
+  const RT* __restrict__ rin;
+  RT* __restrict__ rout;
+  const uint8_t* __restrict__ solid;
+};
+
+// March one work unit (column sg.col, planes [sg.z0, sg.z1)) of a lattice through a full
+// step with the block's TX x TY threads; smem_raw holds step_smem_bytes() bytes.  Ends with
+// a block barrier, so the caller may reuse shared memory right away.
 // REP (CG only): add the repulsion force of Eq. repForce from the pre-pass fields
 // colour / normals (lbm_rep.cuh).
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
-__global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
-    const S* __restrict__ fin, S* __restrict__ fout, const RT* __restrict__ rin, RT* __restrict__ rout,
-    const uint8_t* __restrict__ solid, const int* __restrict__ status, StepParams<T> p,
-    const T* __restrict__ colour, const T* __restrict__ normals, RepParams rp) {
+__device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const StepParams<T>& p,
+                                              const T* __restrict__ colour, const T* __restrict__ normals,
+                                              const RepParams& rp, const Segment& sg,
+                                              unsigned char* __restrict__ smem_raw) {
   constexpr int Q = L::Q;
   constexpr int K = ModelTraits<MODEL>::K, NF = ModelTraits<MODEL>::NF;
   constexpr int NPL = planes_of<L>();
   constexpr int NV = NF + K;  // staged values per ext node: fields, then reference q_k
-  if (status != nullptr && *status != 0) return;  // blown-up state: stop stepping
+  const S* __restrict__ fin = a.fin;
+  S* __restrict__ fout = a.fout;
+  const RT* __restrict__ rin = a.rin;
+  RT* __restrict__ rout = a.rout;
+  const uint8_t* __restrict__ solid = a.solid;
 
   const int TX = blockDim.x, TY = blockDim.y;
   const int EX = TX + 2;
   const int NE = EX * (TY + 2), NI = TX * TY;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const long long N = p.n;
-  int x0 = 0, y0 = 0;
+  const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* fld = reinterpret_cast<T*>(smem_raw);           // [NPL][NV][NE]
   T* pops = fld + NPL * NV * NE;                     // [2][K*Q][NI] deviations
   T* rold = pops + 2 * K * Q * NI;                   // [2][K][NI] old reference densities
@@ -526,8 +542,10 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int e0 = (ty + 1) * EX + (tx + 1);
-  int gx = 0, gy = 0, xm = 0, xp = 0, ym = 0, yp = 0;
-  bool valid = false;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid = gx < p.nx && gy < p.ny;
+  const int xm = gx == 0 ? p.nx - 1 : gx - 1, xp = gx + 1 >= p.nx ? 0 : gx + 1;
+  const int ym = gy == 0 ? p.ny - 1 : gy - 1, yp = gy + 1 >= p.ny ? 0 : gy + 1;
 
   auto collide = [&](int z, int slm, int sl0, int slp, int pb) {
     if (!valid) return;
@@ -590,39 +608,39 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
     }
   };
 
-  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
-  Segment sg;
-  while (work.pop(sg)) {
-    x0 = (sg.col % p.ncx) * TX;
-    y0 = (sg.col / p.ncx) * TY;
-    gx = x0 + tx;
-    gy = y0 + ty;
-    valid = gx < p.nx && gy < p.ny;
-    xm = gx == 0 ? p.nx - 1 : gx - 1;
-    xp = gx + 1 >= p.nx ? 0 : gx + 1;
-    ym = gy == 0 ? p.ny - 1 : gy - 1;
-    yp = gy + 1 >= p.ny ? 0 : gy + 1;
-    const int z0 = sg.z0, z1 = sg.z1;
-    if constexpr (NPL == 3) {
-      stage(z0 - 1, 0, -1);
-      stage(z0, 1, 0);
-      for (int z = z0; z < z1; z++) {
-        const int r = z - z0;
-        const int slm = r % 3, sl0 = (r + 1) % 3, slp = (r + 2) % 3;
-        stage(z + 1, slp, (z + 1 < z1) ? ((r + 1) & 1) : -1);
-        __syncthreads();
-        collide(z, slm, sl0, slp, r & 1);
-        __syncthreads();
-      }
-    } else {
-      for (int z = z0; z < z1; z++) {
-        stage(z, 0, 0);
-        __syncthreads();
-        collide(z, 0, 0, 0, 0);
-        __syncthreads();
-      }
+  const int z0 = sg.z0, z1 = sg.z1;
+  if constexpr (NPL == 3) {
+    stage(z0 - 1, 0, -1);
+    stage(z0, 1, 0);
+    for (int z = z0; z < z1; z++) {
+      const int r = z - z0;
+      const int slm = r % 3, sl0 = (r + 1) % 3, slp = (r + 2) % 3;
+      stage(z + 1, slp, (z + 1 < z1) ? ((r + 1) & 1) : -1);
+      __syncthreads();
+      collide(z, slm, sl0, slp, r & 1);
+      __syncthreads();
+    }
+  } else {
+    for (int z = z0; z < z1; z++) {
+      stage(z, 0, 0);
+      __syncthreads();
+      collide(z, 0, 0, 0, 0);
+      __syncthreads();
     }
   }
+}
+
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
+__global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
+    const S* __restrict__ fin, S* __restrict__ fout, const RT* __restrict__ rin, RT* __restrict__ rout,
+    const uint8_t* __restrict__ solid, const int* __restrict__ status, const __grid_constant__ StepParams<T> p,
+    const T* __restrict__ colour, const T* __restrict__ normals, const __grid_constant__ RepParams rp) {
+  if (status != nullptr && *status != 0) return;  // blown-up state: stop stepping
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const StepArrays<S, RT> a{fin, fout, rin, rout, solid};
+  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
+  Segment sg;
+  while (work.pop(sg)) march_segment<L, T, S, RT, MODEL, WALLS, REP>(a, p, colour, normals, rp, sg, smem_raw);
 }
 
 }  // namespace lbm

@@ -67,6 +67,13 @@ SIGNATURES = {
     "lbm_save_state": (ctypes.c_int, [_VP, _VP]),
     "lbm_load_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "lbm_totals_noalloc": (ctypes.c_int, [ctypes.POINTER(_CParams), _VP, _VP, _VP, _VP]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
+                                        ctypes.POINTER(ctypes.c_size_t), _VP, ctypes.POINTER(_VP)]),
+    "lbm_batch_units": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_set": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "lbm_batch_step": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_batch_launch_count": (ctypes.c_uint64, [_VP]),
+    "lbm_batch_destroy": (ctypes.c_int, [_VP]),
 }
 NOALLOC_MAX_NODES = 1 << 20
 
@@ -82,6 +89,14 @@ def totals_noalloc(params: "Params", pops, solid=None, out=None, stream=None):
     if rc not in (OK, EUNSTABLE):
         raise LbmError(rc, "lbm_totals_noalloc")
     return out, rc
+
+def workspace_bytes(params: "Params") -> int:
+    """Device workspace lbm_create needs for these parameters (size query, no allocation)."""
+    cp = params.to_c()
+    need = ctypes.c_size_t(0)
+    _check(lib().lbm_create(ctypes.byref(cp), None, ctypes.byref(need), None, None), "lbm_create(size)")
+    return int(need.value)
+
 
 _lib = None
 
@@ -287,3 +302,60 @@ class Lattice:
         self._has_walls = solid is not None
         _check(lib().lbm_load_state(self._h, _ptr(state), _ptr(solid)), "lbm_load_state")
         return self
+
+
+class Batch:
+    """Batched stepping of many lattices in one persistent launch per step (lbm_batch_*).
+    The device job table is held as a torch tensor; all jobs must share the batch's stream
+    and storage precision."""
+
+    def __init__(self, precision: int, max_jobs: int, max_units: int, stream=None, device=None):
+        import torch
+        L = lib()
+        need = ctypes.c_size_t(0)
+        _check(L.lbm_batch_create(precision, max_jobs, max_units, None, ctypes.byref(need), None, None),
+               "lbm_batch_create(size)")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.precision = precision
+        self.ws = torch.empty(need.value + 256, dtype=torch.uint8, device=dev)
+        aligned = (self.ws.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        h = ctypes.c_void_p()
+        got = ctypes.c_size_t(need.value)
+        _check(L.lbm_batch_create(precision, max_jobs, max_units, ctypes.c_void_p(aligned), ctypes.byref(got),
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "lbm_batch_create")
+        self._h = h
+        self.jobs = []
+
+    @staticmethod
+    def units(lat: "Lattice") -> int:
+        u = ctypes.c_int32(0)
+        _check(lib().lbm_batch_units(lat._h, ctypes.byref(u)), "lbm_batch_units")
+        return u.value
+
+    def set(self, lattices, nsteps):
+        n = len(lattices)
+        hs = (_VP * max(n, 1))(*[lat._h for lat in lattices])
+        st = (ctypes.c_int32 * max(n, 1))(*[int(k) for k in nsteps])
+        _check(lib().lbm_batch_set(self._h, hs, st, n), "lbm_batch_set")
+        self.jobs = list(lattices)  # keep the contexts alive while they are in the table
+        return self
+
+    def step(self, nsteps: int, graph: bool = True):
+        _check(lib().lbm_batch_step(self._h, int(nsteps), int(bool(graph))), "lbm_batch_step")
+        return self
+
+    def launch_count(self) -> int:
+        return int(lib().lbm_batch_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,246 @@
+"""Serving loop for parameter sweeps: continuous batching of many simulations on one GPU.
+
+A request is one simulation (grid, model, parameters, step count) arriving at some time.
+Two servers answer the same request trace:
+
+* ``PlainServer`` runs the requests one at a time in arrival order, FP32 storage, each
+  lattice stepped with its own tuned kernel (the plain single-simulation path);
+* ``BatchServer`` admits requests as they arrive while the device memory budget and the
+  batch table have room, keeps their lattices resident, and advances all of them together:
+  lattices up to ``batch_max_nodes`` nodes share one persistent batched launch per step
+  (lbm_batch_*, replayed as a CUDA graph per tick of ``tick`` steps), larger ones are
+  stepped with their own tuned kernel on a second stream so their work overlaps the batch.
+  A finished request's moments are read and its memory is released at the end of the
+  tick in which it completes; new requests join at the next tick.
+
+Results are the FP64 totals (lbm_moments) and the component densities; the latency of a
+request is completion minus arrival on a common wall clock.  The physics of a job does
+not depend on what else runs: the batched kernel computes every node with the same code
+whatever the mix.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs, lbm, tune
+
+GRIDS = [(256, 256, 1), (32, 32, 32), (48, 48, 48), (64, 64, 64), (96, 96, 96)]
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the trace start
+    grid: tuple             # (nx, ny, nz); nz == 1 is D2Q9
+    model: int              # lbm.CG or lbm.SC_MP
+    kw: dict                # lbm.Params fields besides lattice/model/precision/grid
+    steps: int
+    seed: int
+
+    @property
+    def nodes(self) -> int:
+        return self.grid[0] * self.grid[1] * self.grid[2]
+
+    def params(self, precision: int) -> "lbm.Params":
+        nx, ny, nz = self.grid
+        lat = lbm.D2Q9 if nz == 1 else lbm.D3Q19
+        return lbm.Params(lattice=lat, model=self.model, precision=precision, nx=nx, ny=ny, nz=nz, **self.kw)
+
+
+def sweep(n: int, seed: int = 5, steps=(5000, 20000), rate_hz: float = 1.0, grids=GRIDS) -> list:
+    """Seeded request trace of a stability-map sweep: grid uniform over `grids`, CG or SC
+    multiphase 50/50, density ratio log-uniform in [1, 1000], viscosity ratio log-uniform
+    in [0.1, 10] (tau_B = 1, tau_R from nu_R), A log-uniform in [1e-4, 1e-1]; SC takes
+    G uniform in the paper's stable window |G| in [4.2, 6.5] (its density ratio follows
+    from G).  Step counts uniform in `steps`; Poisson arrivals at `rate_hz`."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n):
+        t += rng.exponential(1.0 / rate_hz)
+        grid = grids[rng.integers(len(grids))]
+        model = lbm.CG if rng.random() < 0.5 else lbm.SC_MP
+        ratio = 10 ** rng.uniform(0, 3)
+        nu_ratio = 10 ** rng.uniform(-1, 1)
+        nu_b = 1 / 6
+        tau_r = 3 * nu_ratio * nu_b + 0.5
+        if model == lbm.CG:
+            kw = dict(rho_r0=1.0, rho_b0=1.0 / ratio, tau_r=tau_r, tau_b=1.0, A=10 ** rng.uniform(-4, -1))
+        else:
+            kw = dict(G=-rng.uniform(4.2, 6.5), rho0_psi=1.0, tau_r=1.0)
+        out.append(Request(rid, t, grid, model, kw, int(rng.integers(steps[0], steps[1] + 1)), seed * 100003 + rid))
+    return out
+
+
+def initial_fields(req: Request):
+    """Centred droplet of radius L/4 with +-1% seeded noise (SC: liquid 2.0 / gas 0.15)."""
+    nx, ny, nz = req.grid
+    r = min(nx, ny) / 4 if nz == 1 else min(nx, ny, nz) / 4
+    ins = inputs.sphere(nx, ny, nz, r)
+    if req.model == lbm.CG:
+        return inputs.two_fluid(ins, req.kw["rho_r0"], req.kw["rho_b0"], 0.01, req.seed)
+    rho = np.where(ins, 2.0, 0.15) * (1 + 0.01 * inputs.uniform_pm1(req.seed, ins.size))
+    return rho, None
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    start: float
+    done: float
+    status: int
+    totals: dict
+    rho_r: np.ndarray = field(repr=False, default=None)
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def _new_lattice(req: Request, precision: int, stream, tuned: bool):
+    import torch
+    lat = lbm.Lattice(req.params(precision), stream=stream)
+    rr, rb = initial_fields(req)
+    dev = lat.device
+    t = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64).to(dev, non_blocking=False)
+    with torch.cuda.stream(stream):
+        lat.init(t(rr), t(rb))
+    if tuned:
+        tune.autotune(lat)
+    return lat
+
+
+def _finish(lat, req, start, clock, keep_fields):
+    rr = np.empty(req.nodes) if keep_fields else None
+    tot = np.zeros(lbm.NTOTALS)
+    rc = lat.moments_into(rr, None, None, None, tot)   # synchronises the stream
+    return Result(req.rid, req.arrival, start, clock(), rc, dict(zip(lbm.TOTAL_NAMES, tot.tolist())), rr)
+
+
+class PlainServer:
+    """One request at a time, FP32 storage, the lattice's own tuned kernel."""
+
+    def __init__(self, precision: int = lbm.FP32, keep_fields: bool = False):
+        self.precision = precision
+        self.keep_fields = keep_fields
+        self.launches = 0
+
+    def run(self, requests, t0=None):
+        import torch
+        stream = torch.cuda.Stream()
+        t0 = time.perf_counter() if t0 is None else t0
+        clock = lambda: time.perf_counter() - t0
+        out = []
+        for req in sorted(requests, key=lambda r: r.arrival):
+            while clock() < req.arrival:
+                time.sleep(min(1e-3, max(0.0, req.arrival - clock())))
+            start = clock()
+            lat = _new_lattice(req, self.precision, stream, tuned=True)
+            l0 = lat.launch_count()
+            lat.step(req.steps)
+            self.launches += lat.launch_count() - l0
+            out.append(_finish(lat, req, start, clock, self.keep_fields))
+            lat.close()
+        return out
+
+
+class BatchServer:
+    """Continuous batching with HBM-budget admission (see the module docstring)."""
+
+    def __init__(self, precision: int = lbm.FP16, budget_bytes: int = 8 << 30, tick: int = 100,
+                 max_jobs: int = 256, max_units: int = 1 << 16, batch_max_nodes: int = 300_000,
+                 graph: bool = True, keep_fields: bool = False):
+        self.precision = precision
+        self.budget = budget_bytes
+        self.tick = tick
+        self.max_jobs = max_jobs
+        self.max_units = max_units
+        self.batch_max_nodes = batch_max_nodes
+        self.graph = graph
+        self.keep_fields = keep_fields
+        self.launches = 0
+        self.peak_bytes = 0
+        self.peak_jobs = 0
+
+    def run(self, requests, t0=None):
+        import torch
+        small_stream, big_stream = torch.cuda.Stream(), torch.cuda.Stream()
+        batch = lbm.Batch(self.precision, self.max_jobs, self.max_units, stream=small_stream)
+        t0 = time.perf_counter() if t0 is None else t0
+        clock = lambda: time.perf_counter() - t0
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        active = []          # dicts: req, lat, left, start, bytes, small
+        out = []
+        used = 0
+        units_used = 0
+        dirty = False
+        while pending or active:
+            now = clock()
+            # admission: arrived requests, FIFO, while memory and table room remain
+            while pending and pending[0].arrival <= now:
+                req = pending[0]
+                p = req.params(self.precision)
+                need = lbm.workspace_bytes(p)
+                small = req.nodes <= self.batch_max_nodes
+                nu = 0
+                if small:
+                    nx, ny, nz = req.grid
+                    nu = math.ceil(nx / 32) * math.ceil(ny / 8) * (math.ceil(nz / 16) if nz > 1 else 1)
+                if used + need > self.budget or (small and (units_used + nu > self.max_units or
+                                                            sum(a["small"] for a in active) >= self.max_jobs)):
+                    break
+                pending.popleft()
+                lat = _new_lattice(req, self.precision, small_stream if small else big_stream, tuned=not small)
+                active.append(dict(req=req, lat=lat, left=req.steps, start=now, bytes=need, small=small, units=nu))
+                used += need
+                units_used += nu
+                dirty = dirty or small
+            self.peak_bytes = max(self.peak_bytes, used)
+            self.peak_jobs = max(self.peak_jobs, len(active))
+            if not active:
+                if pending:
+                    time.sleep(min(1e-3, max(0.0, pending[0].arrival - clock())))
+                continue
+            smalls = [a for a in active if a["small"]]
+            if dirty:
+                batch.set([a["lat"] for a in smalls], [a["left"] for a in smalls])
+                dirty = False
+            if smalls:
+                batch.step(self.tick, graph=self.graph)
+            for a in active:
+                if not a["small"]:
+                    n = min(self.tick, a["left"])
+                    l0 = a["lat"].launch_count()
+                    a["lat"].step(n)
+                    self.launches += a["lat"].launch_count() - l0
+            small_stream.synchronize()
+            big_stream.synchronize()
+            keep = []
+            for a in active:
+                a["left"] -= min(self.tick, a["left"])
+                if a["left"] == 0:
+                    out.append(_finish(a["lat"], a["req"], a["start"], clock, self.keep_fields))
+                    a["lat"].close()
+                    used -= a["bytes"]
+                    units_used -= a["units"]
+                    dirty = dirty or a["small"]
+                else:
+                    keep.append(a)
+            active = keep
+        self.launches += batch.launch_count()
+        batch.close()
+        return out
+
+
+def summary(results) -> dict:
+    lat = np.array([r.latency for r in results])
+    makespan = max(r.done for r in results) - min(r.arrival for r in results)
+    return {"requests": len(results), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "sims_per_hour": len(results) / makespan * 3600.0, "makespan_s": makespan,
+            "unstable": int(sum(r.status != lbm.OK for r in results))}

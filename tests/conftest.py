@@ -18,3 +18,11 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def lbm():
+    """The CUDA library's binding, built for sm_103a (GPU tests only)."""
+    from paper_2110_05197_gb300 import build, lbm as L
+    build.build()
+    return L

@@ -84,3 +84,21 @@ def test_status_strings(L):
     assert L.lbm_launch_count(None) == 0
     assert L.lbm_step_cg(None, 1) == lbm.EINVAL
     assert L.lbm_moments(None, None, None, None, None, None) == lbm.EINVAL
+
+
+def test_sweep_trace_is_seeded_and_in_range():
+    """The serving sweep's request trace (host only): seeded, parameters in the stated
+    ranges, arrivals increasing."""
+    from paper_2110_05197_gb300 import serve
+    a = serve.sweep(64, seed=5, steps=(5000, 20000), rate_hz=2.0)
+    b = serve.sweep(64, seed=5, steps=(5000, 20000), rate_hz=2.0)
+    assert [(r.grid, r.model, r.steps, r.kw) for r in a] == [(r.grid, r.model, r.steps, r.kw) for r in b]
+    assert all(x.arrival < y.arrival for x, y in zip(a, a[1:]))
+    for r in a:
+        assert r.grid in serve.GRIDS and 5000 <= r.steps <= 20000
+        if r.model == lbm.CG:
+            assert 1e-3 <= r.kw["rho_b0"] <= 1.0 and 1e-4 <= r.kw["A"] <= 1e-1
+            assert 0.5 < r.kw["tau_r"] <= 3 * 10 / 6 + 0.5
+        else:
+            assert 4.2 <= -r.kw["G"] <= 6.5
+    assert {r.model for r in a} == {lbm.CG, lbm.SC_MP}

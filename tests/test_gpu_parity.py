@@ -33,13 +33,6 @@ if not torch.cuda.is_available():  # collected on CPU hosts only to be deselecte
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 
-@pytest.fixture(scope="module")
-def lbm():
-    from paper_2110_05197_gb300 import build, lbm as L
-    build.build()
-    return L
-
-
 def _pops_rel_err(g, o, rho_max, floor=1e-3):
     return np.max(np.abs(g - o) / np.maximum(np.abs(o), floor * rho_max))
 
