@@ -194,6 +194,37 @@ def oracle_sample_mlups(steps: int, nz: int = 16, threads: int | None = None, bu
     return 2 * n * done / dt / 1e6, oracle.get_threads(), dt, n, done
 
 
+def serving_sweep(n_req: int, seed: int = 5):
+    """Continuous-batching sweep (stability-map requests over 2D 256^2 and 32^3..96^3 grids,
+    CG or SC, 200-800 steps each = 1/25 of the 5k-20k of the full sweep).  First a closed
+    batch (every request at t = 0) through the plain FP32 one-at-a-time server measures its
+    service rate mu; then one Poisson trace at 1.2 mu is replayed through both servers."""
+    import torch
+    from paper_2110_05197_gb300 import lbm, serve
+    warm = serve.sweep(10, seed=1, steps=(5, 10), rate_hz=1e6)
+    serve.PlainServer(lbm.FP32).run(warm)           # tunes every grid shape once
+    serve.BatchServer(lbm.FP16, tick=100).run(warm)
+    torch.cuda.synchronize()
+    closed = serve.sweep(n_req, seed=seed, steps=(200, 800), rate_hz=1e6)
+    out = {"requests": n_req, "steps": "U[200, 800] per request (1/25 of the 5k-20k sweep)",
+           "grids": [list(g) for g in serve.GRIDS], "precision": {"plain": "fp32", "batch": "fp16 storage"}}
+    res_plain_closed = serve.PlainServer(lbm.FP32).run(closed)
+    res_batch_closed = serve.BatchServer(lbm.FP16, tick=100).run(closed)
+    pc, bc = serve.summary(res_plain_closed), serve.summary(res_batch_closed)
+    out["closed_batch"] = {"plain_fp32": pc, "batch_fp16": bc, "sims_per_hour_ratio": bc["sims_per_hour"] / pc["sims_per_hour"]}
+    mu = n_req / pc["makespan_s"]
+    trace = serve.sweep(n_req, seed=seed, steps=(200, 800), rate_hz=1.2 * mu)
+    plain_srv, batch_srv = serve.PlainServer(lbm.FP32), serve.BatchServer(lbm.FP16, tick=100)
+    pp = serve.summary(plain_srv.run(trace))
+    bb = serve.summary(batch_srv.run(trace))
+    out["poisson"] = {"rate_hz": 1.2 * mu, "plain_fp32": pp, "batch_fp16": bb,
+                      "sims_per_hour_ratio": bb["sims_per_hour"] / pp["sims_per_hour"],
+                      "batch_peak_resident_jobs": batch_srv.peak_jobs,
+                      "batch_peak_workspace_bytes": batch_srv.peak_bytes,
+                      "launches": {"plain": plain_srv.launches, "batch": batch_srv.launches}}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -349,6 +380,8 @@ def run_ours(args):
             "status": {"cg": lbm.status_string(rc_cg), "sc": lbm.status_string(rc_sc),
                        "cg_mass_r": tot_cg["mass_r"], "sc_mass": tot_sc["mass_r"]},
         }
+        if not args.no_serving and ws == 1:
+            line["serving"] = serving_sweep(args.serving_requests)
         if not args.no_cpu_baseline:
             mlups_cpu, cores, dt, ns, done = oracle_sample_mlups(1, N3, budget_s=10.0)
             line["cpu_baseline"] = {"value": mlups_cpu, "unit": "MLUPS", "cores": cores, "kind": "oracle",
@@ -368,6 +401,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default=None, help="tx,ty,tz for both lattices (default: autotuned)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
+    ap.add_argument("--serving-requests", type=int, default=64)
     ap.add_argument("--profile-only", default=None, choices=["cg", "sc"],
                     help="profiling runs: warm up and step only this lattice, print nothing")
     args = ap.parse_args()

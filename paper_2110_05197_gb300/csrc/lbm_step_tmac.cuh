@@ -11,12 +11,13 @@
 // written by the staging warps straight into the x-neighbours' field slots in distributed
 // shared memory (st.shared::cluster), and announced with a remote mbarrier arrival.
 //
-// Per plane J (slots J % 3 raw, J % 4 fields) the barriers of one block are
+// Per plane J (slots J % RS raw, J % 4 fields; RS = tmac_raw_slots) the barriers of one block are
 //   raw_full  : the producer's tensor copies of the TX interior columns (+ y-halo rows);
 //   raw_free  : 4 staging + 8 collision warps are done with the raw plane;
-//   fld_full  : 4 local staging warps + 4 staging warps of each x-neighbour have written
-//               their part of the field slot (12 arrivals; the remote ones release at
-//               cluster scope, the waits acquire at cluster scope);
+//   fld_full  : the 4 local staging warps and, from each x-neighbour, the staging warp that
+//               wrote its edge column have written their part of the field slot (6
+//               arrivals; the remote ones release at cluster scope, the waits acquire at
+//               cluster scope);
 //   fld_free  : the 8 local collision warps are done with the field slot;
 //   nbr_free  : the 8 collision warps of each x-neighbour are done with their field slot
 //               (16 arrivals), so that this block may write its edge columns into them.
@@ -80,46 +81,71 @@ __device__ __forceinline__ void cluster_sync_all() {
           : "memory");
 }
 
-constexpr int kClusterHeader = 256;  // mbarriers (18 x 8 bytes), 128-byte aligned after it
+constexpr int kClusterHeader = 256;  // mbarriers (up to 24 x 8 bytes), 128-byte aligned after it
 constexpr int kMaxCluster = 8;       // portable cluster size: nx <= 8 * TX
+
+// Two blocks per SM where the shared memory allows it (one population set).
+template <int MODEL>
+__host__ __device__ constexpr int tmac_min_blocks() { return ModelTraits<MODEL>::K == 1 ? 2 : 1; }
+
+// Raw plane buffers: as many as the block's share of shared memory holds, 3 to 6.  The
+// copy of plane J+RS-1 can be issued once plane J's collision has loaded its nodes, so
+// more buffers hide more of the copy latency.
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
+__host__ __device__ constexpr int tmac_raw_slots() {
+  using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
+  constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
+  constexpr size_t budget = tmac_min_blocks<MODEL>() == 1 ? 232448 : 115712;  // per block
+  constexpr size_t fixed = kClusterHeader + kFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kFieldSlots * Lay::NE : 0);
+  constexpr size_t n = (budget - fixed) / Lay::BUF_MAIN;
+  return n > 6 ? 6 : (n < 3 ? 3 : int(n));
+}
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
 __host__ __device__ constexpr size_t tmac_smem_bytes() {
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
-  return kClusterHeader + kRawSlots * Lay::BUF_MAIN + kFieldSlots * NV * Lay::NE * sizeof(T) +
+  constexpr int RS = tmac_raw_slots<L, T, S, RT, MODEL, WALLS, TX, TY>();
+  return kClusterHeader + RS * Lay::BUF_MAIN + kFieldSlots * NV * Lay::NE * sizeof(T) +
          (WALLS ? kFieldSlots * Lay::NE : 0);
 }
 
 // Launch: cluster dims (C, 1, 1) with C = p.ncx = nx / TX; grid = p.nblk clusters * C
 // blocks; p.ncol = ny / TY tile rows (the work partition's columns); cluster c owns the
 // tile-row-planes [c*U/nblk, (c+1)*U/nblk), U = ncol * nz.
-// Two blocks per SM where the shared memory allows it (one population set).
+// Staging warps: 8 for two population sets (the staging of plane J+1 gates the collision
+// of plane J), 4 where two blocks share an SM.
 template <int MODEL>
-__host__ __device__ constexpr int tmac_min_blocks() { return ModelTraits<MODEL>::K == 1 ? 2 : 1; }
+__host__ __device__ constexpr int tmac_stage_warps() { return tmac_min_blocks<MODEL>() == 1 ? 8 : 4; }
+template <int MODEL>
+__host__ __device__ constexpr int tmac_threads() { return 32 * (kCollideWarps + tmac_stage_warps<MODEL>() + 1); }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
-__global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
+__global__ void __launch_bounds__(tmac_threads<MODEL>(), tmac_min_blocks<MODEL>())
     step_kernel_tmac(const __grid_constant__ TmaMaps maps, S* __restrict__ fout, RT* __restrict__ rout,
                      const uint8_t* __restrict__ solid, int* __restrict__ status, StepParams<T> p) {
   static_assert(TX * TY == 32 * kCollideWarps, "one collision thread per tile node");
   static_assert(sizeof(T) == 4, "fields are exchanged as 32-bit words");
+  static_assert(2 * (TY + 2) <= 32, "both edge columns fit the first staging warp's first pass");
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int Q = L::Q, K = Lay::K;
   constexpr int NF = ModelTraits<MODEL>::NF, NV = NF + K;
   constexpr int EX = Lay::EX, NE = Lay::NE;
+  constexpr int kRawSlots = tmac_raw_slots<L, T, S, RT, MODEL, WALLS, TX, TY>();
+  constexpr int kStageWarps = tmac_stage_warps<MODEL>();
+  static_assert(2 * kRawSlots + 3 * kFieldSlots <= kClusterHeader / 8, "mbarriers fit the header");
   // A blown-up (or timed-out) state stops stepping.  Blocks of one cluster may read the
   // word at different times, so none returns here: a skipping block still passes both
   // cluster barriers (its neighbours' waits on it then run out and set the status too).
   const bool skip = *status != 0;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);  // [3]
-  uint64_t* raw_free = raw_full + kRawSlots;                // [3]
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);  // [RS]
+  uint64_t* raw_free = raw_full + kRawSlots;                // [RS]
   uint64_t* fld_full = raw_free + kRawSlots;                // [4]
   uint64_t* fld_free = fld_full + kFieldSlots;              // [4]
   uint64_t* nbr_free = fld_free + kFieldSlots;              // [4]
-  unsigned char* bufs = smem + kClusterHeader;              // [3][BUF_MAIN]
+  unsigned char* bufs = smem + kClusterHeader;              // [RS][BUF_MAIN]
   T* fld = reinterpret_cast<T*>(bufs + kRawSlots * Lay::BUF_MAIN);        // [4][NV][NE]
   uint8_t* msk = reinterpret_cast<uint8_t*>(fld + kFieldSlots * NV * NE);  // [4][NE]
 
@@ -141,7 +167,7 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
       mbar_init(&raw_free[s], kCollideWarps + kStageWarps);
     }
     for (int s = 0; s < kFieldSlots; s++) {
-      mbar_init(&fld_full[s], 3 * kStageWarps);
+      mbar_init(&fld_full[s], kStageWarps + 2);  // local staging warps + one per x-neighbour
       mbar_init(&fld_free[s], kCollideWarps);
       mbar_init(&nbr_free[s], 2 * kCollideWarps);
     }
@@ -213,13 +239,28 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
         }
         const unsigned char* b = bufs + s * Lay::BUF_MAIN;
         const int gz = wrap(z, p.nz);
-        for (int e = stid; e < NE; e += 32 * kStageWarps) {
-          const int ey = e / EX, ex = e - ey * EX;
-          if (WALLS) {
+        if (WALLS) {
+          for (int e = stid; e < NE; e += 32 * kStageWarps) {
+            const int ey = e / EX, ex = e - ey * EX;
             const int gxn = wrap(x0 - 1 + ex, p.nx), gyn = wrap(y0 - 1 + ey, p.ny);
             msk[fs * NE + e] = solid[gxn + (long long)p.nx * (gyn + (long long)p.ny * gz)];
           }
-          if (ex == 0 || ex == TX + 1) continue;  // halo columns: written by the x-neighbours
+        }
+        // Interior columns of all EY rows (the halo columns come from the x-neighbours).  The
+        // two edge columns go first, to staging warp 0, which writes them into the
+        // neighbours' slots early: its release at the end of the plane then finds those
+        // remote stores long completed.
+        for (int it = stid; it < TX * Lay::EY; it += 32 * kStageWarps) {
+          int ex, ey;
+          if (it < 2 * Lay::EY) {
+            ex = it < Lay::EY ? 1 : TX;
+            ey = it < Lay::EY ? it : it - Lay::EY;
+          } else {
+            const int j = it - 2 * Lay::EY;
+            ey = j / (TX - 2);
+            ex = 2 + (j - ey * (TX - 2));
+          }
+          const int e = ey * EX + ex;
           const S* pop = reinterpret_cast<const S*>(b + Lay::PM::row(ey)) + (ex - 1);
           const RT* ref = reinterpret_cast<const RT*>(b + Lay::OFF_RM + Lay::RMR::row(ey)) + (ex - 1);
           T val[NV];
@@ -236,7 +277,7 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
           node_fields<MODEL, T>(p, rho[0], rho[1], val);
 #pragma unroll
           for (int f = 0; f < NV; f++) fld[(fs * NV + f) * NE + e] = val[f];
-          if (ex == 1 || ex == TX) {
+          if (it < 2 * Lay::EY) {
             // edge column: it is the halo column ex' = TX+1 of the left neighbour (ex == 1)
             // or ex' = 0 of the right neighbour (ex == TX)
             const uint32_t peer = ex == 1 ? left : right;
@@ -249,8 +290,10 @@ __global__ void __launch_bounds__(kTmaThreads, tmac_min_blocks<MODEL>())
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&fld_full[fs]);  // local readers: CTA-scope release
-          mbar_arrive_remote(mapa_shared(smem_addr(&fld_full[fs]), left));
-          mbar_arrive_remote(mapa_shared(smem_addr(&fld_full[fs]), right));
+          if (warp == kCollideWarps) {  // the warp that wrote the neighbours' halo columns
+            mbar_arrive_remote(mapa_shared(smem_addr(&fld_full[fs]), left));
+            mbar_arrive_remote(mapa_shared(smem_addr(&fld_full[fs]), right));
+          }
           mbar_arrive(&raw_free[s]);
         }
       }
