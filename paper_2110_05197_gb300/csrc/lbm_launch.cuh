@@ -131,7 +131,7 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(tmac_threads<MODEL>(), 1, 1);
+  cfg.blockDim = dim3(tmac_threads<MODEL, S>(), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = c->stream;
   cfg.attrs = attr;

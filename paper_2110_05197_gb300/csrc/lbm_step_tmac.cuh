@@ -84,9 +84,10 @@ __device__ __forceinline__ void cluster_sync_all() {
 constexpr int kClusterHeader = 256;  // mbarriers (up to 24 x 8 bytes), 128-byte aligned after it
 constexpr int kMaxCluster = 8;       // portable cluster size: nx <= 8 * TX
 
-// Two blocks per SM where the shared memory allows it (one population set).
-template <int MODEL>
-__host__ __device__ constexpr int tmac_min_blocks() { return ModelTraits<MODEL>::K == 1 ? 2 : 1; }
+// Two blocks per SM where the shared memory allows it (one population set, or 16-bit
+// storage).
+template <int MODEL, class S>
+__host__ __device__ constexpr int tmac_min_blocks() { return (ModelTraits<MODEL>::K == 1 || sizeof(S) == 2) ? 2 : 1; }
 
 // Raw plane buffers: as many as the block's share of shared memory holds, 3 to 6.  The
 // copy of plane J+RS-1 can be issued once plane J's collision has loaded its nodes, so
@@ -95,7 +96,7 @@ template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, in
 __host__ __device__ constexpr int tmac_raw_slots() {
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
-  constexpr size_t budget = tmac_min_blocks<MODEL>() == 1 ? 232448 : 115712;  // per block
+  constexpr size_t budget = tmac_min_blocks<MODEL, S>() == 1 ? 232448 : 115712;  // per block
   constexpr size_t fixed = kClusterHeader + kFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kFieldSlots * Lay::NE : 0);
   constexpr size_t n = (budget - fixed) / Lay::BUF_MAIN;
   return n > 6 ? 6 : (n < 3 ? 3 : int(n));
@@ -115,13 +116,13 @@ __host__ __device__ constexpr size_t tmac_smem_bytes() {
 // tile-row-planes [c*U/nblk, (c+1)*U/nblk), U = ncol * nz.
 // Staging warps: 8 for two population sets (the staging of plane J+1 gates the collision
 // of plane J), 4 where two blocks share an SM.
-template <int MODEL>
-__host__ __device__ constexpr int tmac_stage_warps() { return tmac_min_blocks<MODEL>() == 1 ? 8 : 4; }
-template <int MODEL>
-__host__ __device__ constexpr int tmac_threads() { return 32 * (kCollideWarps + tmac_stage_warps<MODEL>() + 1); }
+template <int MODEL, class S>
+__host__ __device__ constexpr int tmac_stage_warps() { return tmac_min_blocks<MODEL, S>() == 1 ? 8 : 4; }
+template <int MODEL, class S>
+__host__ __device__ constexpr int tmac_threads() { return 32 * (kCollideWarps + tmac_stage_warps<MODEL, S>() + 1); }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
-__global__ void __launch_bounds__(tmac_threads<MODEL>(), tmac_min_blocks<MODEL>())
+__global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODEL, S>())
     step_kernel_tmac(const __grid_constant__ TmaMaps maps, S* __restrict__ fout, RT* __restrict__ rout,
                      const uint8_t* __restrict__ solid, int* __restrict__ status, StepParams<T> p) {
   static_assert(TX * TY == 32 * kCollideWarps, "one collision thread per tile node");
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(tmac_threads<MODEL>(), tmac_min_blocks<MODEL>(
   constexpr int NF = ModelTraits<MODEL>::NF, NV = NF + K;
   constexpr int EX = Lay::EX, NE = Lay::NE;
   constexpr int kRawSlots = tmac_raw_slots<L, T, S, RT, MODEL, WALLS, TX, TY>();
-  constexpr int kStageWarps = tmac_stage_warps<MODEL>();
+  constexpr int kStageWarps = tmac_stage_warps<MODEL, S>();
   static_assert(2 * kRawSlots + 3 * kFieldSlots <= kClusterHeader / 8, "mbarriers fit the header");
   // A blown-up (or timed-out) state stops stepping.  Blocks of one cluster may read the
   // word at different times, so none returns here: a skipping block still passes both
