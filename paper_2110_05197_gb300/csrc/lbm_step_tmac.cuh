@@ -11,12 +11,14 @@
 // written by the staging warps straight into the x-neighbours' field slots in distributed
 // shared memory (st.shared::cluster), and announced with a remote mbarrier arrival.
 //
-// Per plane J (slots J % RS raw, J % 4 fields; RS = tmac_raw_slots) the barriers of one block are
+// Per plane J (slots J % RS raw, J % FS fields; RS = tmac_raw_slots, FS = kClusterFieldSlots)
+// the barriers of one block are
 //   raw_full  : the producer's tensor copies of the TX interior columns (+ y-halo rows);
-//   raw_free  : 4 staging + 8 collision warps are done with the raw plane;
-//   fld_full  : the 4 local staging warps and, from each x-neighbour, the staging warp that
-//               wrote its edge column have written their part of the field slot (6
-//               arrivals; the remote ones release at cluster scope, the waits acquire at
+//   raw_free  : the staging warps (tmac_stage_warps) and the 8 collision warps are done
+//               with the raw plane;
+//   fld_full  : the local staging warps and, from each x-neighbour, the staging warp that
+//               wrote its edge column have written their part of the field slot (two
+//               remote arrivals; those release at cluster scope, the waits acquire at
 //               cluster scope);
 //   fld_free  : the 8 local collision warps are done with the field slot;
 //   nbr_free  : the 8 collision warps of each x-neighbour are done with their field slot
@@ -24,7 +26,7 @@
 //               These arrivals are relaxed: they follow the last use of every value read
 //               from the slot, and a release at cluster scope would make the collision warp
 //               wait for its own outstanding global stores.
-// Staging of plane J waits fld_free(J-4) and nbr_free(J-4); collision of plane J waits
+// Staging of plane J waits fld_free(J-FS) and nbr_free(J-FS); collision of plane J waits
 // fld_full of J-1, J, J+1.  No wait is on an earlier plane's event of the same block than
 // the waiter's own, so the pipeline cannot deadlock; every wait is bounded, a timeout sets
 // the status word and the thread skips to the final cluster barrier, which every thread
@@ -83,11 +85,17 @@ __device__ __forceinline__ void cluster_sync_all() {
 
 constexpr int kClusterHeader = 256;  // mbarriers (up to 24 x 8 bytes), 128-byte aligned after it
 constexpr int kMaxCluster = 8;       // portable cluster size: nx <= 8 * TX
+// Field slots: the collision of plane J reads J-1, J, J+1; the others let the staging run
+// ahead by two planes.
+constexpr int kClusterFieldSlots = 5;
 
-// Two blocks per SM where the shared memory allows it (one population set, or 16-bit
-// storage).
+// Blocks per SM: more where the plane buffers are smaller (one population set, 16-bit
+// storage); the step is latency bound, so more resident warps pay even with a few spilled
+// registers.
 template <int MODEL, class S>
-__host__ __device__ constexpr int tmac_min_blocks() { return (ModelTraits<MODEL>::K == 1 || sizeof(S) == 2) ? 2 : 1; }
+__host__ __device__ constexpr int tmac_min_blocks() {
+  return (ModelTraits<MODEL>::K == 1 || sizeof(S) == 2) ? 2 : 1;  // 3 measured no faster
+}
 
 // Raw plane buffers: as many as the block's share of shared memory holds, 3 to 6.  The
 // copy of plane J+RS-1 can be issued once plane J's collision has loaded its nodes, so
@@ -96,8 +104,9 @@ template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, in
 __host__ __device__ constexpr int tmac_raw_slots() {
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
-  constexpr size_t budget = tmac_min_blocks<MODEL, S>() == 1 ? 232448 : 115712;  // per block
-  constexpr size_t fixed = kClusterHeader + kFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kFieldSlots * Lay::NE : 0);
+  // per-block share of the SM's 228 KB (1 KB of it reserved per block), 227 KB at most
+  constexpr size_t budget = tmac_min_blocks<MODEL, S>() == 1 ? 232448 : (233472 / tmac_min_blocks<MODEL, S>() - 1024);
+  constexpr size_t fixed = kClusterHeader + kClusterFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kClusterFieldSlots * Lay::NE : 0);
   constexpr size_t n = (budget - fixed) / Lay::BUF_MAIN;
   return n > 6 ? 6 : (n < 3 ? 3 : int(n));
 }
@@ -107,8 +116,8 @@ __host__ __device__ constexpr size_t tmac_smem_bytes() {
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
   constexpr int RS = tmac_raw_slots<L, T, S, RT, MODEL, WALLS, TX, TY>();
-  return kClusterHeader + RS * Lay::BUF_MAIN + kFieldSlots * NV * Lay::NE * sizeof(T) +
-         (WALLS ? kFieldSlots * Lay::NE : 0);
+  return kClusterHeader + RS * Lay::BUF_MAIN + kClusterFieldSlots * NV * Lay::NE * sizeof(T) +
+         (WALLS ? kClusterFieldSlots * Lay::NE : 0);
 }
 
 // Launch: cluster dims (C, 1, 1) with C = p.ncx = nx / TX; grid = p.nblk clusters * C
@@ -134,7 +143,7 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
   constexpr int EX = Lay::EX, NE = Lay::NE;
   constexpr int kRawSlots = tmac_raw_slots<L, T, S, RT, MODEL, WALLS, TX, TY>();
   constexpr int kStageWarps = tmac_stage_warps<MODEL, S>();
-  static_assert(2 * kRawSlots + 3 * kFieldSlots <= kClusterHeader / 8, "mbarriers fit the header");
+  static_assert(2 * kRawSlots + 3 * kClusterFieldSlots <= kClusterHeader / 8, "mbarriers fit the header");
   // A blown-up (or timed-out) state stops stepping.  Blocks of one cluster may read the
   // word at different times, so none returns here: a skipping block still passes both
   // cluster barriers (its neighbours' waits on it then run out and set the status too).
@@ -143,12 +152,12 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* raw_full = reinterpret_cast<uint64_t*>(smem);  // [RS]
   uint64_t* raw_free = raw_full + kRawSlots;                // [RS]
-  uint64_t* fld_full = raw_free + kRawSlots;                // [4]
-  uint64_t* fld_free = fld_full + kFieldSlots;              // [4]
-  uint64_t* nbr_free = fld_free + kFieldSlots;              // [4]
+  uint64_t* fld_full = raw_free + kRawSlots;                // [kClusterFieldSlots]
+  uint64_t* fld_free = fld_full + kClusterFieldSlots;              // [kClusterFieldSlots]
+  uint64_t* nbr_free = fld_free + kClusterFieldSlots;              // [kClusterFieldSlots]
   unsigned char* bufs = smem + kClusterHeader;              // [RS][BUF_MAIN]
-  T* fld = reinterpret_cast<T*>(bufs + kRawSlots * Lay::BUF_MAIN);        // [4][NV][NE]
-  uint8_t* msk = reinterpret_cast<uint8_t*>(fld + kFieldSlots * NV * NE);  // [4][NE]
+  T* fld = reinterpret_cast<T*>(bufs + kRawSlots * Lay::BUF_MAIN);        // [kClusterFieldSlots][NV][NE]
+  uint8_t* msk = reinterpret_cast<uint8_t*>(fld + kClusterFieldSlots * NV * NE);  // [kClusterFieldSlots][NE]
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -167,7 +176,7 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
       mbar_init(&raw_full[s], 1);
       mbar_init(&raw_free[s], kCollideWarps + kStageWarps);
     }
-    for (int s = 0; s < kFieldSlots; s++) {
+    for (int s = 0; s < kClusterFieldSlots; s++) {
       mbar_init(&fld_full[s], kStageWarps + 2);  // local staging warps + one per x-neighbour
       mbar_init(&fld_free[s], kCollideWarps);
       mbar_init(&nbr_free[s], 2 * kCollideWarps);
@@ -228,11 +237,11 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
     while (ok && work.pop(sg)) {
       const int y0 = sg.col * TY;
       for (int z = sg.z0 - 1; z <= sg.z1; z++, J++) {
-        const int s = J % kRawSlots, fs = J % kFieldSlots;
+        const int s = J % kRawSlots, fs = J % kClusterFieldSlots;
         ok = mbar_wait_bounded(&raw_full[s], (J / kRawSlots) & 1);
-        if (ok && J >= kFieldSlots)
-          ok = mbar_wait_bounded(&fld_free[fs], ((J / kFieldSlots) - 1) & 1) &&
-               mbar_wait_bounded_cluster(&nbr_free[fs], ((J / kFieldSlots) - 1) & 1);
+        if (ok && J >= kClusterFieldSlots)
+          ok = mbar_wait_bounded(&fld_free[fs], ((J / kClusterFieldSlots) - 1) & 1) &&
+               mbar_wait_bounded_cluster(&nbr_free[fs], ((J / kClusterFieldSlots) - 1) & 1);
         ok = __all_sync(0xffffffffu, ok);  // one decision per warp
         if (!ok) {
           give_up();
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
     auto release_fields = [&](int Jf) {
       __syncwarp();
       if (lane == 0) {
-        const int fs = Jf % kFieldSlots;
+        const int fs = Jf % kClusterFieldSlots;
         mbar_arrive(&fld_free[fs]);
         mbar_arrive_remote_relaxed(mapa_shared(smem_addr(&nbr_free[fs]), left));
         mbar_arrive_remote_relaxed(mapa_shared(smem_addr(&nbr_free[fs]), right));
@@ -343,13 +352,13 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
       for (int c = 1; c <= np - 2 && ok; c++) {
         const int Jc = J + c;
         if (c == 1)
-          ok = mbar_wait_bounded_cluster(&fld_full[(Jc - 1) % kFieldSlots], ((Jc - 1) / kFieldSlots) & 1) &&
-               mbar_wait_bounded_cluster(&fld_full[Jc % kFieldSlots], (Jc / kFieldSlots) & 1);
-        ok = ok && mbar_wait_bounded_cluster(&fld_full[(Jc + 1) % kFieldSlots], ((Jc + 1) / kFieldSlots) & 1);
+          ok = mbar_wait_bounded_cluster(&fld_full[(Jc - 1) % kClusterFieldSlots], ((Jc - 1) / kClusterFieldSlots) & 1) &&
+               mbar_wait_bounded_cluster(&fld_full[Jc % kClusterFieldSlots], (Jc / kClusterFieldSlots) & 1);
+        ok = ok && mbar_wait_bounded_cluster(&fld_full[(Jc + 1) % kClusterFieldSlots], ((Jc + 1) / kClusterFieldSlots) & 1);
         ok = ok && mbar_wait_bounded(&raw_full[Jc % kRawSlots], (Jc / kRawSlots) & 1);
         ok = __all_sync(0xffffffffu, ok);  // one decision per warp
         if (!ok) break;
-        const int slm = (Jc - 1) % kFieldSlots, sl0 = Jc % kFieldSlots, slp = (Jc + 1) % kFieldSlots;
+        const int slm = (Jc - 1) % kClusterFieldSlots, sl0 = Jc % kClusterFieldSlots, slp = (Jc + 1) % kClusterFieldSlots;
         const int z = sg.z0 - 1 + c;
         const bool live = !(WALLS && msk[sl0 * NE + e0]);
         T g[K][Q];
