@@ -55,14 +55,18 @@ def sc_kw(n=N3, nz=None):
     return dict(lattice=1, model=1, nx=n, ny=n, nz=nz or n, G=-5.0, rho0_psi=1.0, tau_r=1.0)
 
 
+# Sources that define the FP32 step kernels and their launch (the profiled kernels).
+STEP_KERNEL_SOURCES = ("lbm_lattice.cuh", "lbm_rep.cuh", "lbm_step.cuh", "lbm_step_tma.cuh", "lbm_step_tmac.cuh",
+                       "lbm_launch.cuh", "lbm_internal.cuh", "lbm_step_f32.cu")
+
+
 def csrc_sha256_16():
-    """Hash of the CUDA sources (the kernels whose counters a profile records)."""
-    import glob
+    """Hash of the step kernels' CUDA sources (the kernels whose counters a profile records)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_05197_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
-        with open(f, "rb") as fh:
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -81,6 +81,31 @@ __device__ __forceinline__ int state_index(const lbm_diag* d, int cur) { return 
 template <class S>
 using step_t = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
 
+// Sum of values of the compute type C whose FP64 result is as accurate as FP64 summation.
+// For C = float the sum is carried as an unevaluated pair s + c and the rounding error of
+// every addition is kept exactly (TwoSum), at FP32 cost: GB300's FP64 rate is a small
+// fraction of its FP32 rate, and the reductions here would otherwise be FP64 bound.
+template <class C>
+struct ExactSum;
+template <>
+struct ExactSum<double> {
+  double s = 0.0;
+  __device__ explicit ExactSum(double v = 0.0) : s(v) {}
+  __device__ void add(double v) { s += v; }
+  __device__ double value() const { return s; }
+};
+template <>
+struct ExactSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ explicit ExactSum(float v = 0.f) : s(v) {}
+  __device__ void add(float v) {
+    float e;
+    s = two_sum(s, v, e);
+    c += e;
+  }
+  __device__ double value() const { return double(s) + double(c); }
+};
+
 // 3 sum_i w_i phi(x + c_i) c_i with a wall neighbour replaced by the centre value.
 template <class L, class C>
 __device__ void grad_c(const double* phi, const uint8_t* solid, long long n, int x, int y, int z,
@@ -141,23 +166,22 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
       u[1] = C(U[a.n + n]);
       u[2] = C(U[2 * a.n + n]);
     }
+    C en = C(0);
+    if (a.model == LBM_MODEL_CG && a.enhanced) {
+      const C r = C(rr[n]), b = C(rb[n]), rho = r + b;
+      en = C(1) / ((r / rho) / C(a.nu_r) + (b / rho) / C(a.nu_b));  // Eq. interpVisc
+    }
+    // Only pair 0 is written for fluid nodes: the first step writes every population and
+    // reference density of every fluid node of pair 1.
     for (int k = 0; k < a.K; k++) {
       const double* phi = k == 0 ? rr : rb;
       const RT rref = RT(phi[n]);  // reference density: the initial density, rounded
       C g[3] = {C(0), C(0), C(0)};
-      C en = C(0);
-      if (a.model == LBM_MODEL_CG) {
-        grad_c<L, C>(phi, solid, n, x, y, z, a, g);
-        const double r = rr[n], b = rb[n], rho = r + b;
-        const double nubar = 1.0 / ((r / rho) / a.nu_r + (b / rho) / a.nu_b);  // Eq. interpVisc
-        en = a.enhanced ? C(nubar) : C(0);
-      }
+      if (a.model == LBM_MODEL_CG) grad_c<L, C>(phi, solid, n, x, y, z, a, g);
       feq_dev<L, C>(C(phi[n]), a.phi[k], en, u, g, C(phi[n] - (double)rref), out);
       ra[(long long)k * a.n + n] = rref;
-      rb_[(long long)k * a.n + n] = rref;
       for (int i = 0; i < L::Q; i++) {
         fa[(long long)(k * L::Q + i) * a.n + n] = st_s<S, C>(out[i]);
-        fb[(long long)(k * L::Q + i) * a.n + n] = st_s<S, C>(out[i]);
       }
     }
   }
@@ -215,8 +239,10 @@ __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__
     for (int k = 0; k < 2; k++) {
       double s = 0.0;
       if (k < a.K) {
-        for (int i = 0; i < L::Q; i++) s += to_d(f[(long long)(k * L::Q + i) * a.n + m]);
-        s += to_d(r[(long long)k * a.n + m]);  // sum_i phi_i = 1
+        ExactSum<step_t<S>> acc{static_cast<step_t<S>>(r[(long long)k * a.n + m])};  // sum_i phi_i = 1
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) acc.add(ld_s<S, step_t<S>>(f[(long long)(k * L::Q + i) * a.n + m]));
+        s = acc.value();
       }
       (k == 0 ? rr : rb)[m] = s;
       // Eq. pseudopotential, once per node (the force stencil reads it 18 times)
@@ -281,27 +307,27 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
   acc_init(acc);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
     const bool wall = solid && solid[n];
-    // momentum in FP64: the colours' momenta nearly cancel at interfaces, so summing the
-    // stored values in the compute precision would add its rounding to the reported u
-    double j[3] = {0.0, 0.0, 0.0};
+    // momentum summed exactly (ExactSum): the colours' momenta nearly cancel at
+    // interfaces, so rounding in the sum would show up in the reported u
+    ExactSum<C> jx, jy, jz;
     int bad = 0;
     for (int k = 0; k < a.K; k++) {
       const C rk = C(rref[(long long)k * a.n + n]);
       if (!isfinite(rk)) bad = 1;
-      // the shift phi_i r is symmetric in c_i and carries no momentum: opposite-pair
-      // differences of the stored deviations
+      // the shift phi_i r is symmetric in c_i and carries no momentum: opposite pairs of
+      // the stored deviations
 #pragma unroll
       for (int q = 0; q < L::NP; q++) {
-        const double vp = to_d(f[(long long)(k * L::Q + 2 * q + 1) * a.n + n]);
-        const double vm = to_d(f[(long long)(k * L::Q + 2 * q + 2) * a.n + n]);
+        const C vp = ld_s<S, C>(f[(long long)(k * L::Q + 2 * q + 1) * a.n + n]);
+        const C vm = ld_s<S, C>(f[(long long)(k * L::Q + 2 * q + 2) * a.n + n]);
         if (!isfinite(vp) || !isfinite(vm)) bad = 1;
-        const double dv = vp - vm;
-        if (L::pcx(q)) j[0] += L::pcx(q) * dv;
-        if (L::pcy(q)) j[1] += L::pcy(q) * dv;
-        if (L::pcz(q)) j[2] += L::pcz(q) * dv;
+        if (L::pcx(q)) { jx.add(L::pcx(q) > 0 ? vp : -vp); jx.add(L::pcx(q) > 0 ? -vm : vm); }
+        if (L::pcy(q)) { jy.add(L::pcy(q) > 0 ? vp : -vp); jy.add(L::pcy(q) > 0 ? -vm : vm); }
+        if (L::pcz(q)) { jz.add(L::pcz(q) > 0 ? vp : -vp); jz.add(L::pcz(q) > 0 ? -vm : vm); }
       }
-      if (!isfinite(to_d(f[(long long)(k * L::Q) * a.n + n]))) bad = 1;
+      if (!isfinite(ld_s<S, C>(f[(long long)(k * L::Q) * a.n + n]))) bad = 1;
     }
+    const double j[3] = {jx.value(), jy.value(), jz.value()};
     const double r = rr[n], b = rb[n], rho = r + b;
     double F[3] = {a.body[0], a.body[1], a.body[2]};
     if (!wall && a.model == LBM_MODEL_CG && normals) {
