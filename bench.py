@@ -169,6 +169,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sel), "window": window}
 
 
+def slowest_rank(value: float, device=None) -> float:
+    """Max of a per-rank time over all ranks (the job's time is the slowest replica's);
+    the identity without a process group.  device: where the collective's tensor lives
+    (a CUDA device under NCCL, None = CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank: int, lattices: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas (weak scaling): every rank advances its
+    own `lattices` lattices of `nodes_per_rank` nodes by `steps` steps; `seconds` is the
+    slowest rank's time."""
+    return lattices * nodes_per_rank * steps * world / seconds / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -318,15 +338,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         clk.mark("timed_end")
     launches = cg.launch_count() + sc.launch_count() - l0
-    total_ms = start.elapsed_time(end)
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = slowest_rank(start.elapsed_time(end), dev)
     cg_ms = [a.elapsed_time(b) for a, b, _ in ev]
     sc_ms = [b.elapsed_time(c) for _, b, c in ev]
     cg_avg, sc_avg = float(np.mean(cg_ms)), float(np.mean(sc_ms))
-    value = 2 * n * K * ws / (total_ms / 1e3) / 1e6
+    value = job_mlups(n, 2, K, ws, total_ms / 1e3)
     peak, peak_kind = hbm_peak()
     # 32 x 8 tiles run the cluster TMA kernel on this 128^3 lattice (nx / 32 = 4 <= 8)
     cg_kernel = ("step_kernel_tmac<D3Q19,float,CG>" if list(tiling["cg"][:2]) == [32, 8]
@@ -356,7 +372,7 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     h2d = 3 * n * 8
     d2h = 3 * n * 8 + 2 * lbm.NTOTALS * 8
-    e2e_mlups = 2 * n * K * ws / e2e_s / 1e6
+    e2e_mlups = job_mlups(n, 2, K, ws, slowest_rank(e2e_s, dev))
 
     if rank == 0:
         line = {

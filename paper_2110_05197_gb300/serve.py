@@ -154,7 +154,7 @@ class BatchServer:
     """Continuous batching with HBM-budget admission (see the module docstring)."""
 
     def __init__(self, precision: int = lbm.FP16, budget_bytes: int = 8 << 30, tick: int = 100,
-                 max_jobs: int = 256, max_units: int = 1 << 16, batch_max_nodes: int = 300_000,
+                 max_jobs: int = 256, max_units: int = 1 << 16, batch_max_nodes: int = 120_000,
                  graph: bool = True, keep_fields: bool = False):
         self.precision = precision
         self.budget = budget_bytes
