@@ -118,17 +118,17 @@ def emulsion(nx, ny, nz, count=200, r_mean=10.0, r_spread=2.0, gap=3.0, seed=4, 
                 break
         if ok:
             placed.append((c[0], c[1], c[2], r))
-    x, y, z = grid(nx, ny, nz)
-    inside = np.zeros(x.size, dtype=bool)
+    inside = np.zeros((nz, ny, nx), dtype=bool)
     for (px, py, pz, pr) in placed:
-        dx = np.abs(x - px)
-        dx = np.minimum(dx, nx - dx)
-        dy = np.abs(y - py)
-        dy = np.minimum(dy, ny - dy)
-        dz = np.abs(z - pz)
-        dz = np.minimum(dz, nz - dz)
-        inside |= dx * dx + dy * dy + dz * dz <= pr * pr
-    return inside, placed
+        # the sphere's bounding box, wrapped periodically
+        ix = np.arange(int(np.floor(px - pr)), int(np.ceil(px + pr)) + 1)
+        iy = np.arange(int(np.floor(py - pr)), int(np.ceil(py + pr)) + 1)
+        iz = np.arange(int(np.floor(pz - pr)), int(np.ceil(pz + pr)) + 1)
+        dz, dy, dx = np.meshgrid(iz - pz, iy - py, ix - px, indexing="ij")
+        box = dx * dx + dy * dy + dz * dz <= pr * pr
+        sub = np.ix_(iz % nz, iy % ny, ix % nx)
+        inside[sub] |= box
+    return inside.reshape(-1), placed
 
 
 def channel_walls(nx, ny, nz):
