@@ -185,7 +185,10 @@ bool build_tma_maps(lbm_ctx* c) {
               encode4(fn, &m.ref_main_row, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
                       c->N, kTmaTX, 1) &&
               encode4(fn, &m.ref_main_mid, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
-                      c->N, kTmaTX, kTmaTY);
+                      c->N, kTmaTX, kTmaTY) &&
+              encode4(fn, &m.pop_main_mid4, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, kTmaTX, 4) &&
+              encode4(fn, &m.ref_main_mid4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
+                      c->N, kTmaTX, 4);
     if (!ok) return false;
   }
   return true;

@@ -110,9 +110,9 @@ cudaError_t launch_tma_t(lbm_ctx* c) {
 }
 
 // TMA-staged kernel with the x-halo exchanged inside a cluster of nx / 32 blocks.
-template <class L, class T, class S, class RT, int MODEL, bool WALLS>
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TY>
 cudaError_t launch_tmac_t(lbm_ctx* c) {
-  constexpr int TX = kTmaTX, TY = kTmaTY;
+  constexpr int TX = kTmaTX;
   constexpr size_t smem = tmac_smem_bytes<L, T, S, RT, MODEL, WALLS, TX, TY>();
   auto kern = step_kernel_tmac<L, T, S, RT, MODEL, WALLS, TX, TY>;
   static bool attr_set = false;
@@ -131,7 +131,7 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(tmac_threads<MODEL, S>(), 1, 1);
+  cfg.blockDim = dim3(tmac_threads<MODEL, S, TX, TY>(), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = c->stream;
   cfg.attrs = attr;
@@ -161,9 +161,12 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 cudaError_t launch_step_t(lbm_ctx* c) {
   if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
+    if (c->tma_ok && c->tx == kTmaTX && c->ty == 4 && c->p.nx / kTmaTX <= kMaxCluster &&
+        (long long)c->K * c->Q * c->N < (1LL << 31))
+      return launch_tmac_t<L, T, S, RT, MODEL, WALLS, 4>(c);
     if (c->tma_ok && c->tx == kTmaTX && c->ty == kTmaTY) {
       if (c->p.nx / kTmaTX <= kMaxCluster && (long long)c->K * c->Q * c->N < (1LL << 31))
-        return launch_tmac_t<L, T, S, RT, MODEL, WALLS>(c);
+        return launch_tmac_t<L, T, S, RT, MODEL, WALLS, kTmaTY>(c);
       return launch_tma_t<L, T, S, RT, MODEL, WALLS>(c);
     }
   }

@@ -14,15 +14,15 @@
 // Per plane J (slots J % RS raw, J % FS fields; RS = tmac_raw_slots, FS = kClusterFieldSlots)
 // the barriers of one block are
 //   raw_full  : the producer's tensor copies of the TX interior columns (+ y-halo rows);
-//   raw_free  : the staging warps (tmac_stage_warps) and the 8 collision warps are done
+//   raw_free  : the staging warps (tmac_stage_warps) and the W = TX*TY/32 collision warps are done
 //               with the raw plane;
 //   fld_full  : the local staging warps and, from each x-neighbour, the staging warp that
 //               wrote its edge column have written their part of the field slot (two
 //               remote arrivals; those release at cluster scope, the waits acquire at
 //               cluster scope);
-//   fld_free  : the 8 local collision warps are done with the field slot;
-//   nbr_free  : the 8 collision warps of each x-neighbour are done with their field slot
-//               (16 arrivals), so that this block may write its edge columns into them.
+//   fld_free  : the W local collision warps are done with the field slot;
+//   nbr_free  : the W collision warps of each x-neighbour are done with their field slot
+//               (2W arrivals), so that this block may write its edge columns into them.
 //               These arrivals are relaxed: they follow the last use of every value read
 //               from the slot, and a release at cluster scope would make the collision warp
 //               wait for its own outstanding global stores.
@@ -90,14 +90,16 @@ constexpr int kMaxCluster = 8;       // portable cluster size: nx <= 8 * TX
 constexpr int kClusterFieldSlots = 5;
 
 // Blocks per SM: more where the plane buffers are smaller (one population set, 16-bit
-// storage); the step is latency bound, so more resident warps pay even with a few spilled
-// registers.
-template <int MODEL, class S>
+// storage, 32 x 4 tiles); the step is latency bound, so more resident warps pay even with
+// a few spilled registers.  With 32 x 4 tiles two blocks of half the size share an SM:
+// each cluster's lockstep stalls are then covered by the other cluster's work, which pays
+// where clusters are large (nx = 256: C = 8).
+template <int MODEL, class S, int TY>
 __host__ __device__ constexpr int tmac_min_blocks() {
-  return (ModelTraits<MODEL>::K == 1 || sizeof(S) == 2) ? 2 : 1;  // 3 measured no faster
+  return TY <= 4 ? 2 : ((ModelTraits<MODEL>::K == 1 || sizeof(S) == 2) ? 2 : 1);  // 3 measured no faster
 }
 
-// Raw plane buffers: as many as the block's share of shared memory holds, 3 to 6.  The
+// Raw plane buffers: as many as the block's share of shared memory holds, 2 to 6.  The
 // copy of plane J+RS-1 can be issued once plane J's collision has loaded its nodes, so
 // more buffers hide more of the copy latency.
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
@@ -105,10 +107,10 @@ __host__ __device__ constexpr int tmac_raw_slots() {
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
   // per-block share of the SM's 228 KB (1 KB of it reserved per block), 227 KB at most
-  constexpr size_t budget = tmac_min_blocks<MODEL, S>() == 1 ? 232448 : (233472 / tmac_min_blocks<MODEL, S>() - 1024);
+  constexpr size_t budget = tmac_min_blocks<MODEL, S, TY>() == 1 ? 232448 : (233472 / tmac_min_blocks<MODEL, S, TY>() - 1024);
   constexpr size_t fixed = kClusterHeader + kClusterFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kClusterFieldSlots * Lay::NE : 0);
   constexpr size_t n = (budget - fixed) / Lay::BUF_MAIN;
-  return n > 6 ? 6 : (n < 3 ? 3 : int(n));
+  return n > 6 ? 6 : int(n);
 }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
@@ -125,16 +127,17 @@ __host__ __device__ constexpr size_t tmac_smem_bytes() {
 // tile-row-planes [c*U/nblk, (c+1)*U/nblk), U = ncol * nz.
 // Staging warps: 8 for two population sets (the staging of plane J+1 gates the collision
 // of plane J), 4 where two blocks share an SM.
-template <int MODEL, class S>
-__host__ __device__ constexpr int tmac_stage_warps() { return tmac_min_blocks<MODEL, S>() == 1 ? 8 : 4; }
-template <int MODEL, class S>
-__host__ __device__ constexpr int tmac_threads() { return 32 * (kCollideWarps + tmac_stage_warps<MODEL, S>() + 1); }
+template <int MODEL, class S, int TY>
+__host__ __device__ constexpr int tmac_stage_warps() { return tmac_min_blocks<MODEL, S, TY>() == 1 ? 8 : 4; }
+template <int MODEL, class S, int TX, int TY>
+__host__ __device__ constexpr int tmac_threads() { return TX * TY + 32 * (tmac_stage_warps<MODEL, S, TY>() + 1); }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
-__global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODEL, S>())
+__global__ void __launch_bounds__(tmac_threads<MODEL, S, TX, TY>(), tmac_min_blocks<MODEL, S, TY>())
     step_kernel_tmac(const __grid_constant__ TmaMaps maps, S* __restrict__ fout, RT* __restrict__ rout,
                      const uint8_t* __restrict__ solid, int* __restrict__ status, StepParams<T> p) {
-  static_assert(TX * TY == 32 * kCollideWarps, "one collision thread per tile node");
+  constexpr int kCollideWarps = TX * TY / 32;  // one collision thread per tile node
+  static_assert(TX * TY % 32 == 0, "whole collision warps");
   static_assert(sizeof(T) == 4, "fields are exchanged as 32-bit words");
   static_assert(2 * (TY + 2) <= 32, "both edge columns fit the first staging warp's first pass");
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
@@ -142,7 +145,8 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
   constexpr int NF = ModelTraits<MODEL>::NF, NV = NF + K;
   constexpr int EX = Lay::EX, NE = Lay::NE;
   constexpr int kRawSlots = tmac_raw_slots<L, T, S, RT, MODEL, WALLS, TX, TY>();
-  constexpr int kStageWarps = tmac_stage_warps<MODEL, S>();
+  constexpr int kStageWarps = tmac_stage_warps<MODEL, S, TY>();
+  static_assert(kRawSlots >= 2, "at least two raw plane buffers");
   static_assert(2 * kRawSlots + 3 * kClusterFieldSlots <= kClusterHeader / 8, "mbarriers fit the header");
   // A blown-up (or timed-out) state stops stepping.  Blocks of one cluster may read the
   // word at different times, so none returns here: a skipping block still passes both
@@ -217,8 +221,8 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S>(), tmac_min_blocks<MODE
           for (int g = 0; g < 3; g++) {
             const bool mid = g == 1;
             const int y = g == 0 ? yt : (g == 1 ? y0 : yb);
-            tma_load_4d(b + Lay::PM::group(g), mid ? &maps.pop_main_mid : &maps.pop_main_row, x0, 0, y, gz, bar);
-            tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), mid ? &maps.ref_main_mid : &maps.ref_main_row, x0, 0,
+            tma_load_4d(b + Lay::PM::group(g), mid ? (TY == 4 ? &maps.pop_main_mid4 : &maps.pop_main_mid) : &maps.pop_main_row, x0, 0, y, gz, bar);
+            tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), mid ? (TY == 4 ? &maps.ref_main_mid4 : &maps.ref_main_mid) : &maps.ref_main_row, x0, 0,
                         y, gz, bar);
           }
         }

@@ -152,13 +152,20 @@ def test_tiling_does_not_change_results(lbm, precision, shape):
     tilings, and the TMA-staged kernel (32 x 8 tiles, used for the x % 32 == 0 shapes in
     FP32/FP16; with the x-halo exchanged in a cluster of nx / 32 blocks up to nx = 256, with
     fetched halo columns at nx = 288) for two z-chunk lengths, each also as a persistent
-    grid (tz = 0; at 96 x 64 x 48 every block's share spans several columns).  The two kernels inline the same per-node code but the compiler
-    fuses multiply-adds differently, so across kernels the states agree to a few ulps of
-    the stored deviations."""
+    grid (tz = 0; at 96 x 64 x 48 every block's share spans several columns).  Up to
+    nx = 256 the cluster kernel also runs 32 x 4 tiles (two blocks per SM), which must give
+    the same bits as its 32 x 8 tiles.  The staged and generic kernels inline the same
+    per-node code but the compiler fuses multiply-adds differently, so across kernels the
+    states agree to a few ulps of the stored deviations."""
     case = C.cg_drop3d(*shape)
     tma = shape[0] % 32 == 0 and shape[1] % 8 == 0 and precision != 0
-    generic = [(64, 4, 5), (32, 2, 19), (128, 2, 1), (32, 4, 0), (64, 4, 0)]
+    cluster = tma and shape[0] <= 256
+    generic = [(64, 4, 5), (32, 2, 19), (128, 2, 1), (64, 4, 0)]
     staged = [(32, 8, 16), (32, 8, 3), (32, 8, 0)]
+    if cluster:
+        staged += [(32, 4, 0), (32, 4, 7)]
+    else:
+        generic += [(32, 4, 0)]
     outs = {}
     for tiling in generic + staged:
         lat = C.gpu_lattice(lbm, case, precision)
@@ -174,6 +181,34 @@ def test_tiling_does_not_change_results(lbm, precision, shape):
         scale = np.max(np.abs(outs[generic[0]]))
         print(f"precision {precision}: TMA vs generic max diff {d:.2e} ({d / scale:.2e} of max|f|)")
         assert d <= {1: 1e-6, 2: 2e-4}[precision] * scale
+
+
+@pytest.mark.parametrize("name", ["cg_tma3d", "cg_tma_walls", "sc_tma3d", "sc2c_tma3d"])
+def test_cluster_kernel_32x4_tiles(orc, lbm, name):
+    """The cluster kernel with 32 x 4 tiles (two blocks per SM; the autotuner's pick where
+    clusters are large) against the oracle after 100 FP32 steps, and bit for bit against
+    its 32 x 8 tiles in FP32 and FP16."""
+    case = C.SMALL_CASES[name]()
+    s = C.oracle_sim(orc, case).step(100)
+    for precision in (lbm.FP32, lbm.FP16):
+        a = C.gpu_lattice(lbm, case, precision)
+        b = C.gpu_lattice(lbm, case, precision)
+        a.set_tiling(32, 8, 0)
+        b.set_tiling(32, 4, 0)
+        a.step(100)
+        b.step(100)
+        assert np.array_equal(a.pops().cpu().numpy(), b.pops().cpu().numpy())
+        if precision == lbm.FP32:
+            rr, rb, u, _, rc = b.moments(device=False)
+            orr, orb, ou, _ = s.moments()
+            assert rc == lbm.OK
+            scale = max(orr.max(), orb.max())
+            fl = np.ones(orr.size, bool) if case.solid is None else case.solid == 0
+            er = np.max((np.abs(rr - orr) / np.maximum(np.abs(orr), 1e-3 * scale))[fl])
+            eb = np.max((np.abs(rb - orb) / np.maximum(np.abs(orb), 1e-3 * scale))[fl])
+            eu2 = np.linalg.norm(u - ou) / np.linalg.norm(ou)
+            print(f"{name} 32x4 FP32: rho err {er:.2e}/{eb:.2e}, u err L2 {eu2:.2e}")
+            assert er < 1e-5 and eb < 1e-5 and eu2 < 1e-5
 
 
 def test_deterministic_reruns(lbm):
