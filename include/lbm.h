@@ -67,6 +67,14 @@ enum { LBM_MODEL_CG = 0, LBM_MODEL_SC_MP = 1, LBM_MODEL_SC_2C = 2 };
  * density one step earlier (kept in a reference field, FP64 for LBM_FP64, FP32 otherwise),
  * so 16-bit storage holds only the small non-equilibrium and velocity parts. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
+/* Streaming storage (Eq. streaming).  LBM_STREAM_AB: two population buffers, the step reads
+ * one and pushes into the other.  LBM_STREAM_AA: one buffer updated in place (AA pattern:
+ * even steps write each node's post-collision populations back into its own slots, reversed;
+ * odd steps read from and write to the neighbours' slots), which halves the population
+ * memory; each step then also runs a field pass over the populations (densities and
+ * stencil fields of time t, which the in-place update would otherwise overwrite), so it
+ * moves about 1.5x the bytes.  Results agree with LBM_STREAM_AB to rounding. */
+enum { LBM_STREAM_AB = 0, LBM_STREAM_AA = 1 };
 enum { LBM_NTOTALS = 10 };
 
 /* Parameters of one lattice.  Field meanings follow the paper's notation. */
@@ -94,6 +102,7 @@ typedef struct {
   double body_force[3];   /* constant body-force density (Guo forcing); 0 for none */
   int32_t diag_every;     /* run the blow-up check every n steps inside lbm_step_*; 0 = never */
   double umax_unstable;   /* blow-up threshold on |u| (default used when <= 0: 0.5) */
+  int32_t streaming;      /* LBM_STREAM_AB (0, default) or LBM_STREAM_AA (see above) */
 } lbm_params;
 
 /* Validate p and size the workspace.
@@ -167,8 +176,8 @@ lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t tx, int32_t ty, int32_t tz);
  * together.  The per-node arithmetic is the generic step kernel's, so a lattice's result
  * is bitwise the same alone or in any mix (it may differ by a few ulps from a lattice
  * stepped with lbm_step_* on the TMA-staged kernel).  Jobs must be initialised, periodic
- * (no walls), without the repulsion force, of the batch's storage precision and on the
- * batch's stream.  The periodic diagnostics (diag_every) do not run inside a batch; call
+ * (no walls), without the repulsion force, with two-buffer streaming (LBM_STREAM_AB), of
+ * the batch's storage precision and on the batch's stream.  The periodic diagnostics (diag_every) do not run inside a batch; call
  * lbm_moments per job.
  *
  * lbm_batch_create: precision LBM_FP32, LBM_FP16 or LBM_BF16; capacity max_jobs lattices
@@ -203,7 +212,9 @@ uint64_t lbm_launch_count(const lbm_ctx* ctx);
  * are the portable FP64 form.  lbm_state_bytes: size of that state (0 for NULL).
  * lbm_save_state copies it to dst (host or device, caller-owned, lbm_state_bytes large),
  * synchronously; returns LBM_EUNSTABLE (state still written) if the blow-up check had
- * tripped.  lbm_load_state restores it (solid: the wall mask as for lbm_init_fields, or
+ * tripped.  The state is always written in the two-buffer layout (slot i of node x holds
+ * direction i), also from an in-place context after an odd number of steps, so it loads
+ * into a context of either streaming mode.  lbm_load_state restores it (solid: the wall mask as for lbm_init_fields, or
  * NULL), synchronously, and resets the step counter and blow-up status. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst);

@@ -33,6 +33,7 @@ bool params_ok(const lbm_params* p) {
     if (!(p->rho0_psi > 0)) return false;
   }
   if (p->diag_every < 0) return false;
+  if (p->streaming != LBM_STREAM_AB && p->streaming != LBM_STREAM_AA) return false;
   return true;
 }
 
@@ -87,10 +88,12 @@ size_t workspace_layout(const lbm_params& p, lbm_ctx* c) {
     off += align256(b);
     return o;
   };
+  // in-place streaming: one population buffer and one reference field
+  const bool aa = p.streaming == LBM_STREAM_AA;
   const size_t of0 = take((size_t)K * Q * N * elt);
-  const size_t of1 = take((size_t)K * Q * N * elt);
+  const size_t of1 = aa ? of0 : take((size_t)K * Q * N * elt);
   const size_t or0 = take((size_t)K * N * relt);
-  const size_t or1 = take((size_t)K * N * relt);
+  const size_t or1 = aa ? or0 : take((size_t)K * N * relt);
   const size_t osol = take((size_t)N);
   const size_t ostg = take((size_t)6 * N * sizeof(double));
   const size_t opar = take((size_t)nblk * LBM_NTOTALS * sizeof(double));
@@ -105,6 +108,7 @@ size_t workspace_layout(const lbm_params& p, lbm_ctx* c) {
     c->N = N;
     c->elt = elt;
     c->relt = relt;
+    c->aa = aa;
     c->f[0] = c->ws + of0;
     c->f[1] = c->ws + of1;
     c->r[0] = c->ws + or0;
@@ -169,7 +173,7 @@ static bool encode4(EncodeFn fn, CUtensorMap* m, CUtensorMapDataType dt, size_t 
 
 bool build_tma_maps(lbm_ctx* c) {
   const lbm_params& p = c->p;
-  if (p.lattice != LBM_D3Q19 || p.precision == LBM_FP64) return false;
+  if (p.lattice != LBM_D3Q19 || p.precision == LBM_FP64 || c->aa) return false;
   if (p.nx % kTmaTX != 0 || p.ny % kTmaTY != 0) return false;
   const int K = c->K, Q = c->Q;
   if (K * Q > 256) return false;
@@ -420,7 +424,20 @@ lbm_status lbm_save_state(lbm_ctx* c, void* dst) {
   if (e != cudaSuccess) return fail(c, e);
   const int b = hd.status ? hd.trip_buf : c->cur;
   const size_t fb = (size_t)c->K * c->Q * c->N * c->elt;
-  e = cudaMemcpyAsync(dst, c->f[b], fb, cudaMemcpyDefault, c->stream);
+  if (c->aa && (b & 1)) {
+    // odd in-place layout: gather each population plane into the even (canonical slot)
+    // layout through the staging buffer, so that a saved state always loads at parity 0
+    const size_t pb = (size_t)c->N * c->elt;
+    for (int k = 0; k < c->K && e == cudaSuccess; k++)
+      for (int i = 0; i < c->Q && e == cudaSuccess; i++) {
+        e = lbm::launch_aa_gather_plane(c, c->stage, k, i);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(static_cast<char*>(dst) + (size_t)(k * c->Q + i) * pb, c->stage, pb, cudaMemcpyDefault,
+                              c->stream);
+      }
+  } else {
+    e = cudaMemcpyAsync(dst, c->f[b], fb, cudaMemcpyDefault, c->stream);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(static_cast<char*>(dst) + fb, c->r[b], (size_t)c->K * c->N * c->relt, cudaMemcpyDefault,
                         c->stream);
@@ -443,7 +460,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* src, const uint8_t* solid) {
   }
   const size_t fb = (size_t)c->K * c->Q * N * c->elt;
   const size_t rb = (size_t)c->K * N * c->relt;
-  for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+  for (int b = 0; b < (c->aa ? 1 : 2) && e == cudaSuccess; b++) {
     e = cudaMemcpyAsync(c->f[b], src, fb, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->r[b], static_cast<const char*>(src) + fb, rb, cudaMemcpyDefault, c->stream);

@@ -47,6 +47,7 @@ struct AuxParams {
   double G, rho0;        // SC two-component: G = G_eff
   double body[3];
   double umax, neg_tol;
+  int aa;                // in-place streaming: the state's layout parity is its buffer index
 };
 
 AuxParams aux_params(const lbm_ctx* c) {
@@ -56,6 +57,7 @@ AuxParams aux_params(const lbm_ctx* c) {
   a.ny = q.ny;
   a.nz = q.nz;
   a.n = c->N;
+  a.aa = c->aa;
   a.model = q.model;
   a.enhanced = q.enhanced_eq;
   a.K = c->K;
@@ -151,10 +153,10 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
     if (solid && solid[n]) {
       for (int k = 0; k < a.K; k++) {
         ra[(long long)k * a.n + n] = RT(0);
-        rb_[(long long)k * a.n + n] = RT(0);
+        if (rb_) rb_[(long long)k * a.n + n] = RT(0);
         for (int i = 0; i < L::Q; i++) {
           fa[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(0.0);
-          fb[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(0.0);
+          if (fb) fb[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(0.0);
         }
       }
       continue;
@@ -202,28 +204,41 @@ __global__ void restore_plane_kernel(S* __restrict__ fa, S* __restrict__ fb, RT*
     const RT r = wall ? RT(0) : RT(acc[m]);
     const S v = wall ? from_d<S>(0.0) : from_d<S>(plane[m] - phi * (double)r);
     fa[off + m] = v;
-    fb[off + m] = v;
+    if (fb) fb[off + m] = v;
     if (write_ref) {
       ra[roff + m] = r;
-      rb_[roff + m] = r;
+      if (rb_) rb_[roff + m] = r;
     }
   }
 }
 
-// canonical populations f = g + phi r, FP64; `out` holds planes [first_plane, first_plane+np)
+// canonical populations f = g + phi r, FP64; `out` holds planes [first_plane, first_plane+np);
+// 0 on wall nodes (whose slots the in-place scheme uses for bounced populations)
 template <class L, class S, class RT>
 __global__ void export_kernel(const S* __restrict__ f0, const S* __restrict__ f1, const RT* __restrict__ r0,
                               const RT* __restrict__ r1, const lbm_diag* __restrict__ d, int cur, int first_plane,
-                              int np, double* __restrict__ out, AuxParams a) {
+                              int np, double* __restrict__ out, const uint8_t* __restrict__ solid, AuxParams a) {
   const int b = state_index(d, cur);
   const S* f = b ? f1 : f0;
   const RT* r = b ? r1 : r0;
+  const bool odd = a.aa && (b & 1);
   const long long total = (long long)np * a.n;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < total; m += (long long)gridDim.x * blockDim.x) {
     const int plane = first_plane + (int)(m / a.n);
     const long long node = m - (long long)(plane - first_plane) * a.n;
     const int k = plane / L::Q, i = plane - k * L::Q;
-    out[m] = to_d(f[(long long)plane * a.n + node]) + a.phi[k][grp<L>(i)] * to_d(r[(long long)k * a.n + node]);
+    out[m] = (solid && solid[node]) ? 0.0
+                                    : to_d(f[aa_index_n<L>(k, i, node, a.nx, a.ny, a.nz, a.n, odd)]) +
+                                          a.phi[k][grp<L>(i)] * to_d(r[(long long)k * a.n + node]);
+  }
+}
+
+// stored plane (k, i) of the even layout from the odd in-place layout (0 on wall nodes)
+template <class L, class S>
+__global__ void aa_gather_kernel(const S* __restrict__ f, S* __restrict__ out, const uint8_t* __restrict__ solid,
+                                 int k, int i, AuxParams a) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+    out[m] = (solid && solid[m]) ? from_d<S>(0.0) : f[aa_index_n<L>(k, i, m, a.nx, a.ny, a.nz, a.n, true)];
   }
 }
 
@@ -235,13 +250,15 @@ __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__
   const int b = state_index(d, cur);
   const S* f = b ? f1 : f0;
   const RT* r = b ? r1 : r0;
+  const bool odd = a.aa && (b & 1);
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
     for (int k = 0; k < 2; k++) {
       double s = 0.0;
       if (k < a.K) {
         ExactSum<step_t<S>> acc{static_cast<step_t<S>>(r[(long long)k * a.n + m])};  // sum_i phi_i = 1
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) acc.add(ld_s<S, step_t<S>>(f[(long long)(k * L::Q + i) * a.n + m]));
+        for (int i = 0; i < L::Q; i++)
+          acc.add(ld_s<S, step_t<S>>(f[aa_index_n<L>(k, i, m, a.nx, a.ny, a.nz, a.n, odd)]));
         s = acc.value();
       }
       (k == 0 ? rr : rb)[m] = s;
@@ -303,6 +320,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
   const int bsel = state_index(d, cur);
   const S* f = bsel ? f1 : f0;
   const RT* rref = bsel ? r1 : r0;
+  const bool odd = a.aa && (bsel & 1);
   Acc acc;
   acc_init(acc);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
@@ -318,8 +336,8 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
       // the stored deviations
 #pragma unroll
       for (int q = 0; q < L::NP; q++) {
-        const C vp = ld_s<S, C>(f[(long long)(k * L::Q + 2 * q + 1) * a.n + n]);
-        const C vm = ld_s<S, C>(f[(long long)(k * L::Q + 2 * q + 2) * a.n + n]);
+        const C vp = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 1, n, a.nx, a.ny, a.nz, a.n, odd)]);
+        const C vm = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 2, n, a.nx, a.ny, a.nz, a.n, odd)]);
         if (!isfinite(vp) || !isfinite(vm)) bad = 1;
         if (L::pcx(q)) { jx.add(L::pcx(q) > 0 ? vp : -vp); jx.add(L::pcx(q) > 0 ? -vm : vm); }
         if (L::pcy(q)) { jy.add(L::pcy(q) > 0 ? vp : -vp); jy.add(L::pcy(q) > 0 ? -vm : vm); }
@@ -426,9 +444,10 @@ int grid_for(long long n, int threads, int cap) {
 template <class L, class S, class RT>
 cudaError_t init_t(lbm_ctx* c, const double* rr, const double* rb, const double* u) {
   const AuxParams a = aux_params(c);
+  // in-place streaming: one buffer pair (the second pointers alias the first)
   init_eq_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
-      static_cast<S*>(c->f[0]), static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]), static_cast<RT*>(c->r[1]), rr,
-      rb, u, c->has_walls ? c->solid : nullptr, a);
+      static_cast<S*>(c->f[0]), c->aa ? nullptr : static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]),
+      c->aa ? nullptr : static_cast<RT*>(c->r[1]), rr, rb, u, c->has_walls ? c->solid : nullptr, a);
   return cudaGetLastError();
 }
 
@@ -437,7 +456,8 @@ cudaError_t restore_t(lbm_ctx* c, const double* plane, int k, int i, const doubl
   double phi[2][3];
   rest_weights(c->p, phi);
   restore_plane_kernel<S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
-      static_cast<S*>(c->f[0]), static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]), static_cast<RT*>(c->r[1]),
+      static_cast<S*>(c->f[0]), c->aa ? nullptr : static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]),
+      c->aa ? nullptr : static_cast<RT*>(c->r[1]),
       plane, acc + (long long)k * c->N, c->has_walls ? c->solid : nullptr, c->N, (long long)(k * c->Q + i) * c->N,
       (long long)k * c->N, phi[k][grp<L>(i)], i == 0);
   return cudaGetLastError();
@@ -448,7 +468,15 @@ cudaError_t export_t(lbm_ctx* c, double* out, int first_plane, int np) {
   const AuxParams a = aux_params(c);
   export_kernel<L, S, RT><<<grid_for((long long)np * c->N, 256, 16384), 256, 0, c->stream>>>(
       static_cast<const S*>(c->f[0]), static_cast<const S*>(c->f[1]), static_cast<const RT*>(c->r[0]),
-      static_cast<const RT*>(c->r[1]), c->diag, c->cur, first_plane, np, out, a);
+      static_cast<const RT*>(c->r[1]), c->diag, c->cur, first_plane, np, out, c->has_walls ? c->solid : nullptr, a);
+  return cudaGetLastError();
+}
+
+template <class L, class S, class RT>
+cudaError_t gather_t(lbm_ctx* c, void* out, int k, int i) {
+  const AuxParams a = aux_params(c);
+  aa_gather_kernel<L, S><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
+      static_cast<const S*>(c->f[0]), static_cast<S*>(out), c->has_walls ? c->solid : nullptr, k, i, a);
   return cudaGetLastError();
 }
 
@@ -513,6 +541,10 @@ struct ExportOp {
   static cudaError_t run(lbm_ctx* c, double* out, int first, int np) { return export_t<L, S, RT>(c, out, first, np); }
 };
 template <class L, class S, class RT>
+struct GatherOp {
+  static cudaError_t run(lbm_ctx* c, void* out, int k, int i) { return gather_t<L, S, RT>(c, out, k, i); }
+};
+template <class L, class S, class RT>
 struct DiagOp {
   static cudaError_t run(lbm_ctx* c, double* uo) { return diag_t<L, S, RT>(c, uo); }
 };
@@ -543,6 +575,11 @@ cudaError_t launch_export_plane(lbm_ctx* c, double* plane, int k, int i) {
 cudaError_t launch_export_all(lbm_ctx* c, double* pops) {
   c->launches += 1;
   return by_lattice_precision<ExportOp>(c, pops, 0, c->K * c->Q);
+}
+
+cudaError_t launch_aa_gather_plane(lbm_ctx* c, void* out, int k, int i) {
+  c->launches += 1;
+  return by_lattice_precision<GatherOp>(c, out, k, i);
 }
 
 cudaError_t launch_diagnostics(lbm_ctx* c, double* u_out, bool want_u) {

@@ -31,9 +31,12 @@ struct lbm_ctx {
   void* f[2];            // A/B population buffers [K][Q][N], deviations from phi * r
   void* r[2];            // A/B reference densities [K][N] (paired with f[])
   int cur;               // index of the buffer pair holding the current state
+  bool aa;               // in-place streaming: f[1] == f[0], r[1] == r[0], and cur is the
+                         // layout parity of the state (lbm_step_aa.cuh)
   uint8_t* solid;        // [N] wall mask (all zero without walls)
   bool has_walls;
-  double* stage;         // [6][N] FP64 staging: rho_r, rho_b, u_x, u_y, u_z, psi (SC multiphase)
+  double* stage;         // [6][N] FP64 staging: rho_r, rho_b, u_x, u_y, u_z, psi (SC multiphase);
+                         // in-place streaming also uses it for the step's field pass
   double* partials;      // [nblk_diag][LBM_NTOTALS]
   int nblk_diag;
   lbm_diag* diag;        // device
@@ -78,6 +81,9 @@ cudaError_t launch_restore_accumulate(lbm_ctx* c, const double* plane, int k, do
 cudaError_t launch_restore_plane(lbm_ctx* c, const double* plane, int k, int i, const double* acc);
 cudaError_t launch_export_plane(lbm_ctx* c, double* plane, int k, int i);
 cudaError_t launch_export_all(lbm_ctx* c, double* pops);
+// In-place streaming at odd parity: stored plane (k, i) of the even layout into out [N]
+// (storage type), i.e. slot opp(i) of node x - c_i for every x.
+cudaError_t launch_aa_gather_plane(lbm_ctx* c, void* out, int k, int i);
 // Densities into stage[0..2N), velocity into u_out (or stage[2N..5N) when null and
 // want_u), block partials, then the fixed-order final reduction into c->diag.
 cudaError_t launch_diagnostics(lbm_ctx* c, double* u_out, bool want_u);

@@ -5,20 +5,22 @@
 #include <algorithm>
 
 #include "lbm_internal.cuh"
+#include "lbm_step_aa.cuh"
 #include "lbm_step_tmac.cuh"
 
 namespace lbm {
 
-// rho^N for the repulsion pre-pass, with the step's density bookkeeping
+// rho^N for the repulsion pre-pass, with the step's density bookkeeping; odd: the state
+// is in the odd in-place layout
 template <class L, class T, class S, class RT>
 __global__ void colour_kernel(const S* __restrict__ f, const RT* __restrict__ r, T* __restrict__ colour,
-                              RepParams a) {
+                              RepParams a, int odd) {
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
     T rho[2];
     for (int k = 0; k < 2; k++) {
       T g[L::Q];
 #pragma unroll
-      for (int i = 0; i < L::Q; i++) g[i] = ld_s<S, T>(f[(long long)(k * L::Q + i) * a.n + m]);
+      for (int i = 0; i < L::Q; i++) g[i] = ld_s<S, T>(f[aa_index_n<L>(k, i, m, a.nx, a.ny, a.nz, a.n, odd)]);
       rho[k] = comp_state<L, T, RT>(g, T(r[(long long)k * a.n + m])).rho;
     }
     T s0 = rho[0], s1 = rho[1];
@@ -54,7 +56,7 @@ cudaError_t launch_rep_prepass_t(lbm_ctx* c, int buf) {
   const int grid = (int)std::min<long long>((c->N + 255) / 256, 8192);
   colour_kernel<L, T, S, RT><<<grid, 256, 0, c->stream>>>(static_cast<const S*>(c->f[buf]),
                                                            static_cast<const RT*>(c->r[buf]),
-                                                           static_cast<T*>(c->colour), a);
+                                                           static_cast<T*>(c->colour), a, c->aa ? (buf & 1) : 0);
   normals_kernel<L, T><<<grid, 256, 0, c->stream>>>(static_cast<const T*>(c->colour),
                                                     c->has_walls ? c->solid : nullptr, static_cast<T*>(c->normals), a);
   c->launches += 2;
@@ -158,8 +160,34 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
   return cudaLaunchKernelEx(&cfg, kern, c->tma[c->cur], fout, rout, c->solid, &c->diag->status, sp);
 }
 
+// In-place (AA) step: the field pass, then the step kernel, both over all nodes.
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
+cudaError_t launch_aa_t(lbm_ctx* c) {
+  if constexpr (REP) {
+    cudaError_t e = launch_rep_prepass_t<L, T, S, RT>(c, c->cur);
+    if (e != cudaSuccess) return e;
+  }
+  const StepParams<T> sp = make_step_params<T>(c);
+  const int odd = c->cur & 1;
+  S* f = static_cast<S*>(c->f[0]);
+  RT* r = static_cast<RT*>(c->r[0]);
+  T* fld = reinterpret_cast<T*>(c->stage);  // [NF + K][N] of the compute type, fits 6N doubles
+  const long long blocks = (c->N + 255) / 256;
+  const int grid = (int)std::min<long long>(blocks, (long long)c->nsm * 16);
+  aa_fields_kernel<L, T, S, RT, MODEL><<<grid, 256, 0, c->stream>>>(f, r, fld, WALLS ? c->solid : nullptr,
+                                                                   &c->diag->status, sp, odd);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  c->launches += 1;
+  aa_step_kernel<L, T, S, RT, MODEL, WALLS, REP><<<grid, 256, 0, c->stream>>>(
+      f, r, fld, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour), static_cast<const T*>(c->normals),
+      rep_params(c), odd);
+  return cudaGetLastError();
+}
+
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 cudaError_t launch_step_t(lbm_ctx* c) {
+  if (c->aa) return launch_aa_t<L, T, S, RT, MODEL, WALLS, REP>(c);
   if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
     if (c->tma_ok && c->tx == kTmaTX && c->ty == 4 && c->p.nx / kTmaTX <= kMaxCluster &&
         (long long)c->K * c->Q * c->N < (1LL << 31))

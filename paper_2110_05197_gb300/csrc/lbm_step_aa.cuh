@@ -1,0 +1,148 @@
+// In-place streaming (AA pattern): one population buffer instead of two.
+//
+// Storage.  After an even number of steps the canonical population f^k_i(x) sits in slot i
+// of node x; after an odd number, in slot opp(i) of node x - c_i.  An even step reads the
+// node's own slots and writes post-collision f*_i to slot opp(i) of the same node; an odd
+// step reads slot opp(i) of x - c_i and writes f*_i to slot i of x + c_i.  In both steps a
+// node reads and writes the same Q locations per component and no other node touches them,
+// so the update is race-free in place.  Halfway bounce-back (Eq. streaming with walls:
+// f_opp(i)(x, t+1) = f*_i(x) when x + c_i is a wall node) goes, in an even step, to slot i
+// of the wall node x + c_i (whence the next odd step reads it back as f_opp(i)(x)), and in
+// an odd step to slot opp(i) of x; both locations belong to no other fluid node.
+// Deviations (g = f - phi_i q) are re-referenced to the destination node's q exactly as in
+// the two-buffer scheme; the reference densities are read and rewritten by their own node
+// only, so they are updated in place as well.
+//
+// The stencils need the densities of the 18 neighbours at time t, which a neighbour may
+// already have overwritten in place.  A first pass therefore writes every node's stencil
+// fields and reference densities (NF + K values of the compute type) into a field array,
+// and the step kernel reads its neighbours' values from there: 2*K*Q populations plus
+// K*Q more per node for the pass, i.e. 1.5x the bytes of a two-buffer step, for half the
+// population memory.
+#pragma once
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+// Index of the canonical population f^k_i at node n = x + nx (y + ny z) in the in-place
+// buffer after an even (odd == false) or odd number of steps.
+template <class L>
+__device__ __forceinline__ long long aa_index(int k, int i, long long n, int x, int y, int z, int nx, int ny, int nz,
+                                              long long N, bool odd) {
+  if (!odd || i == 0) return (long long)(k * L::Q + i) * N + n;
+  return (long long)(k * L::Q + opp<L>(i)) * N + wrap_index(x - cx<L>(i), y - cy<L>(i), z - cz<L>(i), nx, ny, nz);
+}
+
+template <class L>
+__device__ __forceinline__ long long aa_index_n(int k, int i, long long n, int nx, int ny, int nz, long long N,
+                                                bool odd) {
+  if (!odd || i == 0) return (long long)(k * L::Q + i) * N + n;
+  const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+  return aa_index<L>(k, i, n, x, y, z, nx, ny, nz, N, odd);
+}
+
+// Field pass: fld[NF + K][N] = the stencil fields (node_fields) and the new reference
+// densities q_k of every fluid node, from the state at t (layout parity `odd`).
+template <class L, class T, class S, class RT, int MODEL>
+__global__ void __launch_bounds__(256) aa_fields_kernel(const S* __restrict__ f, const RT* __restrict__ r,
+                                                        T* __restrict__ fld, const uint8_t* __restrict__ solid,
+                                                        const int* __restrict__ status, const StepParams<T> p,
+                                                        int odd) {
+  if (*status != 0) return;  // blown-up state: stop stepping
+  constexpr int Q = L::Q, K = ModelTraits<MODEL>::K, NF = ModelTraits<MODEL>::NF;
+  const long long N = p.n;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    if (solid && solid[n]) continue;  // wall values are never read: the stencil substitutes the centre
+    const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+    T rho[2] = {T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      T v[Q];
+#pragma unroll
+      for (int i = 0; i < Q; i++) v[i] = ld_s<S, T>(f[aa_index<L>(k, i, n, x, y, z, p.nx, p.ny, p.nz, N, odd)]);
+      const CompState<T> c = comp_state<L, T, RT>(v, T(r[(long long)k * N + n]));
+      rho[k] = c.rho;
+      fld[(long long)(NF + k) * N + n] = c.q;
+    }
+    T out[2];
+    node_fields<MODEL, T>(p, rho[0], rho[1], out);
+#pragma unroll
+    for (int fi = 0; fi < NF; fi++) fld[(long long)fi * N + n] = out[fi];
+  }
+}
+
+// One in-place step (layout parity `odd` at t), one thread per node: moments, stencil from
+// the field pass, collision (the same per-node code as the two-buffer kernels), streaming.
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
+__global__ void __launch_bounds__(256, min_blocks<T>())
+    aa_step_kernel(S* __restrict__ f, RT* __restrict__ r, const T* __restrict__ fld,
+                   const uint8_t* __restrict__ solid, const int* __restrict__ status,
+                   const __grid_constant__ StepParams<T> p, const T* __restrict__ colour,
+                   const T* __restrict__ normals, const __grid_constant__ RepParams rp, int odd) {
+  if (*status != 0) return;
+  constexpr int Q = L::Q, K = ModelTraits<MODEL>::K, NF = ModelTraits<MODEL>::NF;
+  const long long N = p.n;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    if (WALLS && solid[n]) continue;
+    const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+    const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x + 1 >= p.nx ? 0 : x + 1;
+    const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y + 1 >= p.ny ? 0 : y + 1;
+    const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z + 1 >= p.nz ? 0 : z + 1;
+    auto nb = [&](int i) -> long long {
+      const int X = cx<L>(i) == 0 ? x : (cx<L>(i) > 0 ? xp : xm);
+      const int Y = cy<L>(i) == 0 ? y : (cy<L>(i) > 0 ? yp : ym);
+      const int Z = cz<L>(i) == 0 ? z : (cz<L>(i) > 0 ? zp : zm);
+      return X + (long long)p.nx * (Y + (long long)p.ny * Z);
+    };
+    // x - c_i = the neighbour in direction opp(i)
+    T g[K][Q];
+    CompState<T> cs[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+#pragma unroll
+      for (int i = 0; i < Q; i++) {
+        const long long src = (odd && i != 0) ? (long long)(k * Q + opp<L>(i)) * N + nb(opp<L>(i))
+                                              : (long long)(k * Q + i) * N + n;
+        g[k][i] = ld_s<S, T>(f[src]);
+      }
+      cs[k] = comp_state<L, T, RT>(g[k], T(r[(long long)k * N + n]));
+    }
+    auto nbr = [&](int fi, int i) -> T {
+      const long long m = nb(i);
+      if (WALLS && solid[m]) return fld[(long long)fi * N + n];
+      return fld[(long long)fi * N + m];
+    };
+    if constexpr (MODEL == kCG) {
+      T Fx[3] = {T(0), T(0), T(0)};
+      if constexpr (REP) rep_force<L, T>(normals, colour, WALLS ? solid : nullptr, x, y, z, rp, Fx);
+      cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
+    } else if constexpr (MODEL == kSCMP) {
+      scmp_collide<L, T>(p, g, cs[0], nbr);
+    } else {
+      sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) r[(long long)k * N + n] = RT(cs[k].q);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const long long d = nb(i);
+      const bool bounce = WALLS && i != 0 && solid[d];
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        T v = g[k][i];
+        if (i != 0 && !bounce) v += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(long long)(NF + k) * N + d]);
+        long long dst;
+        if (i == 0)
+          dst = (long long)(k * Q) * N + n;
+        else if (!odd)
+          dst = bounce ? (long long)(k * Q + i) * N + d : (long long)(k * Q + opp<L>(i)) * N + n;
+        else
+          dst = bounce ? (long long)(k * Q + opp<L>(i)) * N + n : (long long)(k * Q + i) * N + d;
+        f[dst] = st_s<S, T>(v);
+      }
+    }
+  }
+}
+
+}  // namespace lbm

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 D2Q9, D3Q19 = 0, 1
 CG, SC_MP, SC_2C = 0, 1, 2
 FP64, FP32, FP16, BF16 = 0, 1, 2, 3
+STREAM_AB, STREAM_AA = 0, 1
 NTOTALS = 10
 TOTAL_NAMES = ("mass_r", "mass_b", "mom_x", "mom_y", "mom_z", "e_kin", "max_u", "nonfinite",
                "min_rho_r", "min_rho_b")
@@ -47,6 +48,7 @@ class _CParams(ctypes.Structure):
         ("body_force", ctypes.c_double * 3),
         ("diag_every", ctypes.c_int32),
         ("umax_unstable", ctypes.c_double),
+        ("streaming", ctypes.c_int32),
     ]
 
 
@@ -155,6 +157,7 @@ class Params:
     body_force: tuple = (0.0, 0.0, 0.0)
     diag_every: int = 0
     umax_unstable: float = 0.5
+    streaming: int = 0          # STREAM_AB (two buffers) or STREAM_AA (in place)
 
     def to_c(self) -> _CParams:
         p = _CParams()

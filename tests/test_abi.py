@@ -65,12 +65,16 @@ def test_workspace_size_query(L):
     assert b - b16 == 2 * 2 * 19 * N * 2
     rc, bsc = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP32, model=lbm.SC_MP)
     assert b - bsc == 2 * 19 * N * 4 + 2 * N * 4
+    # in-place streaming keeps one population buffer and one reference field
+    rc, baa = _size(L, nx=128, ny=128, nz=128, precision=lbm.FP32, model=lbm.CG, streaming=lbm.STREAM_AA)
+    assert rc == lbm.OK and b - baa == (pops + ref) // 2
 
 
 @pytest.mark.parametrize("bad", [
     dict(nx=0), dict(lattice=lbm.D2Q9, nz=4), dict(tau_r=0.5), dict(precision=4), dict(model=9),
     dict(rho_b0=-1.0), dict(model=lbm.SC_MP, rho0_psi=0.0), dict(diag_every=-1),
     dict(rho_r0=0.1, rho_b0=1.0),  # alpha_R < 0 from Eq. gamma
+    dict(streaming=2),
 ])
 def test_invalid_parameters_rejected(L, bad):
     rc, _ = _size(L, **bad)
