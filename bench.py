@@ -249,6 +249,31 @@ def serving_sweep(n_req: int, seed: int = 5):
     return out
 
 
+def in_place_steps(rr, rb, rho, dev, stream, steps: int = 20):
+    """Step times of the same two lattices with in-place (AA) streaming: one population
+    buffer, a field pass plus the step kernel per step (not part of `value`)."""
+    import torch
+    from paper_2110_05197_gb300 import lbm
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    out = {"bytes_moved_per_lu": {"cg": 2 * 19 * 4 + 8 + 16 + 2 * (2 * 19 * 4 + 8) + 16,
+                                  "sc": 19 * 4 + 4 + 8 + 2 * (19 * 4 + 4) + 8}}
+    for name, kw, fields in (("cg", cg_kw(), (rr, rb)), ("sc", sc_kw(), (rho,))):
+        lat = lbm.Lattice(lbm.Params(precision=lbm.FP32, streaming=lbm.STREAM_AA, **kw), stream=stream)
+        lat.init(*(t(f) for f in fields))
+        lat.step(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[f"{name}_step_ms"] = ms
+        out[f"{name}_mlups"] = N3 ** 3 / (ms / 1e3) / 1e6
+        out[f"{name}_status"] = lbm.status_string(lat.totals()[1])
+        lat.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -350,6 +375,7 @@ def run_ours(args):
     achieved = BYTES_PER_LU["cg"] * n / (cg_avg / 1e3) / 1e9
     tot_cg, rc_cg = cg.totals()
     tot_sc, rc_sc = sc.totals()
+    in_place = in_place_steps(rr, rb, rho, dev, stream)
 
     # end to end through the public API with pinned host buffers: init from host fields,
     # K CG + K SC steps, densities and totals back to the host
@@ -397,6 +423,7 @@ def run_ours(args):
                     "request": f"init from pinned host fields + {K} CG and {K} SC steps + densities/totals to host"},
             "gpu_launches": launches,
             "tiling": tiling,
+            "in_place": in_place,
             "status": {"cg": lbm.status_string(rc_cg), "sc": lbm.status_string(rc_sc),
                        "cg_mass_r": tot_cg["mass_r"], "sc_mass": tot_sc["mass_r"]},
         }
