@@ -142,7 +142,7 @@ lbm_status lbm_step_sc(lbm_ctx* ctx, int32_t nsteps);
  *   E_kin = sum 1/2 rho |u|^2, max |u|, count of nodes with a non-finite population,
  *   min rho_r, min rho_b -- over fluid nodes, reduced in FP64 in a fixed order.
  * totals != NULL synchronises the stream and returns LBM_EUNSTABLE when the blow-up check
- * trips (a non-finite population, a density below -1e-6 times the larger bulk density, or
+ * trips (a non-finite population, a density below -1e-2 times the larger bulk density, or
  * max|u| > umax_unstable), also when a
  * periodic in-step check (diag_every) tripped earlier. */
 lbm_status lbm_moments(lbm_ctx* ctx, double* rho_r, double* rho_b, double* u, double* pops,

@@ -70,7 +70,7 @@ AuxParams aux_params(const lbm_ctx* c) {
   a.umax = q.umax_unstable > 0 ? q.umax_unstable : 0.5;
   double scale = 1.0;
   if (q.model == LBM_MODEL_CG) scale = fmax(scale, fmax(q.rho_r0, q.rho_b0));
-  a.neg_tol = 1e-6 * scale;
+  a.neg_tol = kNegDensityTol * scale;
   return a;
 }
 

@@ -58,6 +58,12 @@ struct lbm_ctx {
 namespace lbm {
 
 constexpr int kDiagThreads = 256;
+// Blow-up check: a density below -kNegDensityTol times the larger bulk density (at least 1)
+// trips it.  Recolouring moves populations of a colour across a sharp interface with
+// either sign, so that colour's density can dip a few 1e-6 below zero on the far side
+// (seen at density ratio 12 with A = 0.3); a deficit of a percent only comes from a
+// diverging run.
+constexpr double kNegDensityTol = 1e-2;
 
 // Workspace layout; returns the total size.  All regions 256-byte aligned.
 size_t workspace_layout(const lbm_params& p, lbm_ctx* c /* may be null: size only */);

@@ -225,7 +225,7 @@ extern "C" lbm_status lbm_totals_noalloc(const lbm_params* p, const double* pops
   a.rho0 = p->rho0_psi;
   for (int d = 0; d < 3; d++) a.body[d] = p->body_force[d];
   a.umax = p->umax_unstable > 0 ? p->umax_unstable : 0.5;
-  a.neg_tol = 1e-6 * (p->model == LBM_MODEL_CG ? fmax(1.0, fmax(p->rho_r0, p->rho_b0)) : 1.0);
+  a.neg_tol = lbm::kNegDensityTol * (p->model == LBM_MODEL_CG ? fmax(1.0, fmax(p->rho_r0, p->rho_b0)) : 1.0);
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int g1 = (int)std::min<long long>((n + kThreads - 1) / kThreads, 8192);

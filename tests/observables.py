@@ -47,6 +47,19 @@ def radius_along_x(rho_r, rho_b, shape) -> float:
     return 0.5 * float(cr[-1] - cr[0])
 
 
+def endpoint_along_z(rho_r, rho_b, shape) -> float:
+    """Position of the upper rho^N = 0 crossing on the z line through the box centre,
+    relative to the centre plane (linear interpolation between nodes); shape = (nz, ny, nx)."""
+    nz, ny, nx = shape
+    col = colour(rho_r, rho_b).reshape(shape)
+    line = col[:, ny // 2, nx // 2]
+    idx = np.nonzero(np.diff((line > 0).astype(np.int8)))[0]
+    if len(idx) == 0:
+        return float("nan")
+    i = idx[-1]
+    return float(i + line[i] / (line[i] - line[i + 1]) - (nz - 1) / 2.0)
+
+
 def oscillation_frequency(r, dt: float) -> float:
     """Angular frequency of a decaying oscillation r(t) sampled every dt steps, from a
     least-squares fit of c + a exp(-g t) cos(w t + p); the zero crossings of r - mean(r)
