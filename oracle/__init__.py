@@ -21,7 +21,7 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 
 D2Q9, D3Q19 = 0, 1
-CG, SC_MP, SC_2C = 0, 1, 2
+CG, SC_MP, SC_2C, SC_MR = 0, 1, 2, 3
 NTOTALS = 10
 TOTAL_NAMES = ("mass_r", "mass_b", "mom_x", "mom_y", "mom_z", "e_kin", "max_u", "nonfinite",
                "min_rho_r", "min_rho_b")
@@ -54,6 +54,7 @@ class _Params(ctypes.Structure):
         ("grad_eps", ctypes.c_double),
         ("G", ctypes.c_double), ("rho0_psi", ctypes.c_double),
         ("body_force", ctypes.c_double * 3),
+        ("Ga", ctypes.c_double * 2), ("Gr", ctypes.c_double * 2),
     ]
 
 
@@ -79,6 +80,8 @@ def lib():
         L.orc_lattice_tables.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), dp, dp, dp, dp]
         L.orc_phi.argtypes = [ctypes.c_int, ctypes.c_double, dp]
+        L.orc_mr_vectors.argtypes = [ctypes.POINTER(ctypes.c_int), dp]
+        L.orc_mr_vectors.restype = ctypes.c_int
         L.orc_cg_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp,
                                          ctypes.c_double, ctypes.c_int, dp]
         L.orc_sc_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
@@ -99,6 +102,15 @@ def _p(a):
 
 def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def mr_vectors():
+    """The 93 vectors of belts 1 and 2 and their weights p (Eq. pweights), as the oracle
+    uses them: (c [93, 3] int, p [93])."""
+    c = np.zeros(93 * 3, dtype=np.int32)
+    p = np.zeros(93)
+    m = lib().orc_mr_vectors(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(p))
+    return c.reshape(-1, 3)[:m], p[:m]
 
 
 def set_threads(n: int) -> None:
@@ -189,13 +201,15 @@ class Params:
     G: float = 0.0
     rho0_psi: float = 1.0
     body_force: tuple = (0.0, 0.0, 0.0)
+    Ga: tuple = (0.0, 0.0)       # SC_MR: attractive self-couplings G^a of species A, B
+    Gr: tuple = (0.0, 0.0)       # SC_MR: repulsive self-couplings G^r of species A, B
 
     def to_c(self) -> _Params:
         p = _Params()
         for f in fields(self):
             v = getattr(self, f.name)
-            if f.name == "body_force":
-                p.body_force = (ctypes.c_double * 3)(*[float(x) for x in v])
+            if f.name in ("body_force", "Ga", "Gr"):
+                setattr(p, f.name, (ctypes.c_double * len(v))(*[float(x) for x in v]))
             else:
                 setattr(p, f.name, v)
         return p

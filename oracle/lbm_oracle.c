@@ -21,6 +21,10 @@
  *     collisSC, equiliSC, source), streaming (Eq. streamingSC).
  *   SC two-component: cross force of Eq. doublebeltrepulsionforce2 between the two
  *     species, common velocity, per-species BGK + source.
+ *   SC multicomponent with multirange potentials (Eq. benziforces): per species the
+ *     attractive belt-1 force (Eq. doublebeltattractiveforce), the repulsive belt-1 + belt-2
+ *     force with the weights p of Eq. pweights (Eq. doublebeltrepulsionforce) and the
+ *     cross force of Eq. doublebeltrepulsionforce2; then as the two-component model.
  *
  * Readings where the paper is silent, garbled or ambiguous (stated once here):
  *   - Perturbation: applied as A/2 |grad rho^N| [w_i (c_i.grad rho^N)^2/|grad rho^N|^2 - B_i]
@@ -38,6 +42,10 @@
  *   - Two-component SC: common barycentric velocity, each species relaxes with its own tau.
  *   - D2Q9 constants (the paper prints D3Q19 only) are chosen to satisfy the same moment
  *     identities as the D3Q19 set.
+ *   - Multirange SC: belt 1 of the attractive and cross forces is the lattice's own 18
+ *     neighbours with the weights w_i (D3Q19 has no (1,1,1) vectors, whose w would be 0);
+ *     the repulsive force runs over all 92 non-zero vectors with |c|^2 <= 8 (belts 1 and 2)
+ *     with p; Psi_s = rho_0 (1 - exp(-rho_s / rho_0)) as Eq. pseudopotential, per species.
  */
 #include "lbm_oracle.h"
 
@@ -205,7 +213,7 @@ struct orc_sim {
   double phiR[19], phiB[19];
   double *f, *fpost;
   uint8_t* solid;
-  double *rho_r, *rho_b, *color, *gN, *gR, *gB, *F, *psi;
+  double *rho_r, *rho_b, *color, *gN, *gR, *gB, *F, *psi, *psi2;  /* gN: 2nd species force for SC */
 };
 
 static int g_threads = 0;
@@ -246,6 +254,7 @@ orc_sim* orc_create(const orc_params* p) {
   if (!p || p->nx <= 0 || p->ny <= 0 || p->nz <= 0) return NULL;
   if (p->lattice != ORC_D2Q9 && p->lattice != ORC_D3Q19) return NULL;
   if (p->lattice == ORC_D2Q9 && p->nz != 1) return NULL;
+  if (p->model == ORC_SC_MR && p->lattice != ORC_D3Q19) return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof *s);
   s->p = *p;
   lattice_fill(p->lattice, &s->L);
@@ -264,6 +273,7 @@ orc_sim* orc_create(const orc_params* p) {
   s->rho_b = (double*)calloc(s->n, sizeof(double));
   s->color = (double*)calloc(s->n, sizeof(double));
   s->psi = (double*)calloc(s->n, sizeof(double));
+  s->psi2 = (double*)calloc(s->n, sizeof(double));
   s->gN = (double*)calloc(3 * s->n, sizeof(double));
   s->gR = (double*)calloc(3 * s->n, sizeof(double));
   s->gB = (double*)calloc(3 * s->n, sizeof(double));
@@ -280,6 +290,7 @@ void orc_destroy(orc_sim* s) {
   free(s->rho_b);
   free(s->color);
   free(s->psi);
+  free(s->psi2);
   free(s->gN);
   free(s->gR);
   free(s->gB);
@@ -448,6 +459,48 @@ static void stage_stream(orc_sim* s) {
 /* Eq. pseudopotential. */
 static double sc_psi(double rho, double rho0) { return rho0 * (1.0 - exp(-rho / rho0)); }
 
+/* Belts 1 and 2 (Eq. pweights): every integer vector with |c|^2 <= 8, ordered by |c|^2
+ * (rest first), and its weight p, which depends only on |c|^2. */
+static int mr_table(int c[93][3], double p[93]) {
+  int m = 0;
+  for (int r2 = 0; r2 <= 8; r2++) {
+    double w;
+    switch (r2) {
+      case 0: w = 0.0; break;
+      case 1: w = 4.0 / 135.0; break;
+      case 2: w = 1.0 / 63.0; break;
+      case 3: w = 2.0 / 315.0; break;
+      case 4: w = 5.0 / 1512.0; break;
+      case 5: w = 1.0 / 945.0; break;
+      case 6: w = 1.0 / 1890.0; break;
+      case 8: w = 1.0 / 15120.0; break;
+      default: continue; /* no integer vector has |c|^2 = 7 */
+    }
+    for (int x = -2; x <= 2; x++)
+      for (int y = -2; y <= 2; y++)
+        for (int z = -2; z <= 2; z++)
+          if (x * x + y * y + z * z == r2) {
+            c[m][0] = x;
+            c[m][1] = y;
+            c[m][2] = z;
+            p[m] = w;
+            m++;
+          }
+  }
+  return m;
+}
+
+int orc_mr_vectors(int* c, double* p) {
+  int cc[93][3];
+  double pp[93];
+  int m = mr_table(cc, pp);
+  for (int j = 0; j < m; j++) {
+    for (int a = 0; a < 3; a++) c[3 * j + a] = cc[j][a];
+    p[j] = pp[j];
+  }
+  return m;
+}
+
 /* SC forces for every node into s->F (Eq. interactionforceMP, or the cross force of
  * Eq. doublebeltrepulsionforce2 for the two-component model: species 0 -> F, species 1 ->
  * the second half of gN, reused as scratch). */
@@ -465,6 +518,51 @@ static void stage_sc_force(orc_sim* s) {
         for (int a = 0; a < 3; a++) acc[a] += L->w[i] * v * L->c[i][a];
       }
       for (int a = 0; a < 3; a++) s->F[3 * n + a] = -s->p.G * s->psi[n] * acc[a] + s->p.body_force[a];
+    }
+  } else if (s->p.model == ORC_SC_MR) {
+    /* Eq. benziforces per species s: F^a_s + F^r_s + F^X_s (+ its share of the body force) */
+    const double g = s->p.G / (s->p.rho0_psi * s->p.rho0_psi);
+    int c[93][3];
+    double pw[93];
+    const int nv = mr_table(c, pw);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < (long)s->n; n++) {
+      s->psi[n] = sc_psi(s->rho_r[n], s->p.rho0_psi);
+      s->psi2[n] = sc_psi(s->rho_b[n], s->p.rho0_psi);
+    }
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < (long)s->n; n++) {
+      long x, y, z;
+      coords(s, (size_t)n, &x, &y, &z);
+      const double* psis[2] = {s->psi, s->psi2};
+      const double* rhos[2] = {s->rho_r, s->rho_b};
+      const double rho = s->rho_r[n] + s->rho_b[n];
+      for (int sp = 0; sp < 2; sp++) {
+        const double* ps = psis[sp];
+        const double* other = rhos[1 - sp];
+        double att[3] = {0.0, 0.0, 0.0}, rep[3] = {0.0, 0.0, 0.0}, crs[3] = {0.0, 0.0, 0.0};
+        /* belt 1 with the lattice weights: Eq. doublebeltattractiveforce and the cross
+           force of Eq. doublebeltrepulsionforce2 */
+        for (int i = 1; i < L->q; i++) {
+          size_t m = neighbour(s, (size_t)n, i);
+          double vp = s->solid[m] ? ps[n] : ps[m];
+          double vo = s->solid[m] ? other[n] : other[m];
+          for (int a = 0; a < 3; a++) {
+            att[a] += L->w[i] * vp * L->c[i][a];
+            crs[a] += L->w[i] * vo * L->c[i][a];
+          }
+        }
+        /* belts 1 + 2 with the weights p: Eq. doublebeltrepulsionforce */
+        for (int j = 1; j < nv; j++) {
+          size_t m = node_of(s, x + c[j][0], y + c[j][1], z + c[j][2]);
+          double vp = s->solid[m] ? ps[n] : ps[m];
+          for (int a = 0; a < 3; a++) rep[a] += pw[j] * vp * c[j][a];
+        }
+        double* out = sp == 0 ? s->F + 3 * n : s->gN + 3 * n;
+        for (int a = 0; a < 3; a++)
+          out[a] = -s->p.Ga[sp] * ps[n] * att[a] - s->p.Gr[sp] * ps[n] * rep[a] - g * rhos[sp][n] * crs[a] +
+                   s->p.body_force[a] * rhos[sp][n] / rho;
+      }
     }
   } else {
     double g = s->p.G / (s->p.rho0_psi * s->p.rho0_psi);
@@ -624,7 +722,7 @@ int orc_moments(orc_sim* s, double* rho_r, double* rho_b, double* u, double* tot
     double rr = s->rho_r[n], rb = s->rho_b[n], rho = rr + rb;
     double Ft[3];
     for (int a = 0; a < 3; a++) Ft[a] = s->F[3 * n + a];
-    if (s->p.model == ORC_SC_2C)
+    if (s->p.model == ORC_SC_2C || s->p.model == ORC_SC_MR)
       for (int a = 0; a < 3; a++) Ft[a] += s->gN[3 * n + a];
     for (int a = 0; a < 3; a++) un[a] = s->solid[n] ? 0.0 : (j[a] + 0.5 * Ft[a]) / rho;
     if (rho_r) rho_r[n] = rr;

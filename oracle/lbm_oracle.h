@@ -30,7 +30,7 @@ extern "C" {
 #endif
 
 enum { ORC_D2Q9 = 0, ORC_D3Q19 = 1 };
-enum { ORC_CG = 0, ORC_SC_MP = 1, ORC_SC_2C = 2 };
+enum { ORC_CG = 0, ORC_SC_MP = 1, ORC_SC_2C = 2, ORC_SC_MR = 3 };
 enum { ORC_NTOTALS = 10 };
 
 typedef struct {
@@ -49,6 +49,9 @@ typedef struct {
   double G, rho0_psi;    /* SC coupling and reference density (Eqs. interactionforceMP, pseudopotential,
                             doublebeltrepulsionforce2) */
   double body_force[3];  /* constant body-force density, applied with Guo forcing */
+  double Ga[2], Gr[2];   /* ORC_SC_MR (D3Q19 only): attractive and repulsive self-couplings of
+                            each species (Eqs. doublebeltattractiveforce,
+                            doublebeltrepulsionforce); G is the cross coupling G_AB */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -73,6 +76,9 @@ int orc_moments(orc_sim* s, double* rho_r, double* rho_b, double* u, double* tot
 int orc_force(orc_sim* s, double* F);
 
 /* ---- per-node building blocks, exported for the identity tests ---- */
+/* The 93 vectors of belts 1 and 2 (every integer vector with |c|^2 <= 8, rest first) and
+ * their forcing weights p (Eq. pweights): c[93][3], p[93].  Returns 93. */
+int orc_mr_vectors(int* c, double* p);
 int orc_lattice_tables(int lattice, int* q, int* c, double* w, double* B, double* psi,
                        double* xi);
 void orc_phi(int lattice, double alpha, double* phi);

@@ -65,7 +65,7 @@ def unshift(a, c):
 @dataclass
 class Params:
     d3: bool
-    model: str                 # "cg", "sc_mp", "sc_2c"
+    model: str                 # "cg", "sc_mp", "sc_2c", "sc_mr"
     shape: tuple               # (nz, ny, nx)
     rho_r0: float = 1.0
     rho_b0: float = 1.0
@@ -83,7 +83,26 @@ class Params:
     G: float = 0.0
     rho0: float = 1.0
     body: tuple = (0.0, 0.0, 0.0)
+    Ga: tuple = (0.0, 0.0)     # sc_mr: attractive self-couplings (belt 1, weights w)
+    Gr: tuple = (0.0, 0.0)     # sc_mr: repulsive self-couplings (belts 1 + 2, weights p)
     solid: np.ndarray | None = None
+
+
+# Eq. pweights: the forcing weight of a belt vector depends on |c|^2 only
+P_OF_R2 = {1: 4 / 135, 2: 1 / 63, 3: 2 / 315, 4: 5 / 1512, 5: 1 / 945, 6: 1 / 1890, 8: 1 / 15120}
+
+
+def belt_vectors():
+    """Non-zero integer vectors of belts 1 and 2 (|c|^2 <= 8) with their weights p."""
+    r = np.arange(-2, 3)
+    out = []
+    for x in r:
+        for y in r:
+            for z in r:
+                r2 = int(x * x + y * y + z * z)
+                if r2 in P_OF_R2:
+                    out.append(((int(x), int(y), int(z)), P_OF_R2[r2]))
+    return out
 
 
 class BruteForce:
@@ -248,10 +267,37 @@ class BruteForce:
             post[1, i] = fs - post[0, i]
         return post
 
+    def _weighted_sum(self, s, vectors):
+        """sum_j wt_j s(x + c_j) c_j over (c, wt) pairs; a solid neighbour gives s(x)."""
+        acc = np.zeros((3,) + s.shape)
+        for c, wt in vectors:
+            v = np.where(shift(self.solid, c), s, shift(s, c))
+            for a in range(3):
+                if c[a]:
+                    acc[a] += wt * v * c[a]
+        return acc
+
     def sc_post(self):
         p, L, f = self.p, self.L, self.f
         rhos = [f[k].sum(axis=0) for k in range(self.K)]
         body = self.body_field()
+        if p.model == "sc_mr":
+            # Eq. benziforces: attractive belt 1 (w), repulsive belts 1+2 (p), cross (w)
+            lattice = [(L.c[i], L.w[i]) for i in range(1, L.q)]
+            belts = belt_vectors()
+            rho = rhos[0] + rhos[1]
+            Fs = []
+            for k in range(2):
+                Psi = p.rho0 * (1 - np.exp(-rhos[k] / p.rho0))
+                Fa = -p.Ga[k] * Psi * self._weighted_sum(Psi, lattice)
+                Fr = -p.Gr[k] * Psi * self._weighted_sum(Psi, belts)
+                Fx = -(p.G / p.rho0 ** 2) * rhos[k] * self._weighted_sum(rhos[1 - k], lattice)
+                Fs.append(Fa + Fr + Fx + body * rhos[k] / rho)
+            u = (self.momentum(f) + 0.5 * sum(Fs)) / rho
+            post = np.empty_like(f)
+            for k, tau in enumerate((p.tau_r, p.tau_b)):
+                post[k] = f[k] - (f[k] - self.sc_feq(rhos[k], u)) / tau + self.guo(u, Fs[k], 1 / tau)
+            return post
         if p.model == "sc_mp":
             rho = rhos[0]
             psi = p.rho0 * (1 - np.exp(-rho / p.rho0))
