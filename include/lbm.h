@@ -61,7 +61,7 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
-enum { LBM_MODEL_CG = 0, LBM_MODEL_SC_MP = 1, LBM_MODEL_SC_2C = 2 };
+enum { LBM_MODEL_CG = 0, LBM_MODEL_SC_MP = 1, LBM_MODEL_SC_2C = 2, LBM_MODEL_SC_MR = 3 };
 /* Storage precision of the populations.  FP64 computes in FP64; the others compute in FP32.
  * Populations are stored as deviations from the rest-state equilibrium of each node's
  * density one step earlier (kept in a reference field, FP64 for LBM_FP64, FP32 otherwise),
@@ -80,7 +80,8 @@ enum { LBM_NTOTALS = 10 };
 /* Parameters of one lattice.  Field meanings follow the paper's notation. */
 typedef struct {
   int32_t lattice;        /* LBM_D2Q9 (nz must be 1) or LBM_D3Q19 */
-  int32_t model;          /* LBM_MODEL_CG, LBM_MODEL_SC_MP (one set), LBM_MODEL_SC_2C (two sets) */
+  int32_t model;          /* LBM_MODEL_CG, LBM_MODEL_SC_MP (one set), LBM_MODEL_SC_2C (two sets),
+                             LBM_MODEL_SC_MR (two sets, multirange potentials; D3Q19 only) */
   int32_t precision;      /* LBM_FP64, LBM_FP32, LBM_FP16 or LBM_BF16 (see above) */
   int32_t nx, ny, nz;     /* lattice size, each >= 1; periodic in every direction */
   double rho_r0, rho_b0;  /* CG bulk densities; density ratio gamma = rho_r0/rho_b0 (Eq. gamma) */
@@ -103,6 +104,16 @@ typedef struct {
   int32_t diag_every;     /* run the blow-up check every n steps inside lbm_step_*; 0 = never */
   double umax_unstable;   /* blow-up threshold on |u| (default used when <= 0: 0.5) */
   int32_t streaming;      /* LBM_STREAM_AB (0, default) or LBM_STREAM_AA (see above) */
+  double Ga[2], Gr[2];    /* LBM_MODEL_SC_MR (Sec. 2.1, Eq. benziforces): per species the
+                             attractive belt-1 coupling G^a (lattice weights w, Eq.
+                             doublebeltattractiveforce) and the repulsive belts-1+2 coupling
+                             G^r (weights p of Eq. pweights over the 92 vectors with
+                             |c|^2 <= 8, Eq. doublebeltrepulsionforce), acting on
+                             Psi_s = rho0_psi (1 - exp(-rho_s / rho0_psi)); G is the cross
+                             coupling G_AB of Eq. doublebeltrepulsionforce2.  The model steps
+                             with lbm_step_sc on the field-pass kernels (its force reaches
+                             distance 2), in either streaming mode; the batched launch and
+                             lbm_totals_noalloc do not take it. */
 } lbm_params;
 
 /* Validate p and size the workspace.

@@ -16,7 +16,9 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 bool params_ok(const lbm_params* p) {
   if (!p) return false;
   if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return false;
-  if (p->model < LBM_MODEL_CG || p->model > LBM_MODEL_SC_2C) return false;
+  if (p->model < LBM_MODEL_CG || p->model > LBM_MODEL_SC_MR) return false;
+  // the multirange model's repulsion reaches distance 2 (D3Q19 belts)
+  if (p->model == LBM_MODEL_SC_MR && (p->lattice != LBM_D3Q19 || p->nx < 2 || p->ny < 2 || p->nz < 2)) return false;
   if (p->precision < LBM_FP64 || p->precision > LBM_BF16) return false;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
   if (p->lattice == LBM_D2Q9 && p->nz != 1) return false;

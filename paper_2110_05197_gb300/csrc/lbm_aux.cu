@@ -47,6 +47,7 @@ struct AuxParams {
   double G, rho0;        // SC two-component: G = G_eff
   double body[3];
   double umax, neg_tol;
+  double Ga[2], Gr[2];   // multirange SC self-couplings
   int aa;                // in-place streaming: the state's layout parity is its buffer index
 };
 
@@ -64,7 +65,11 @@ AuxParams aux_params(const lbm_ctx* c) {
   rest_weights(q, a.phi);
   a.nu_r = (q.tau_r - 0.5) / 3.0;
   a.nu_b = (q.tau_b - 0.5) / 3.0;
-  a.G = q.model == LBM_MODEL_SC_2C ? q.G / (q.rho0_psi * q.rho0_psi) : q.G;
+  a.G = (q.model == LBM_MODEL_SC_2C || q.model == LBM_MODEL_SC_MR) ? q.G / (q.rho0_psi * q.rho0_psi) : q.G;
+  for (int k = 0; k < 2; k++) {
+    a.Ga[k] = q.Ga[k];
+    a.Gr[k] = q.Gr[k];
+  }
   a.rho0 = q.rho0_psi;
   for (int d = 0; d < 3; d++) a.body[d] = q.body_force[d];
   a.umax = q.umax_unstable > 0 ? q.umax_unstable : 0.5;
@@ -383,6 +388,37 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
           F[dd] = -a.G * psic * s1[dd] + a.body[dd];
         else
           F[dd] = -a.G * r * s1[dd] - a.G * b * s2[dd] + a.body[dd];
+      }
+      if (a.model == LBM_MODEL_SC_MR) {
+        // self forces of Eqs. doublebeltattractiveforce / doublebeltrepulsionforce with
+        // Psi_s = rho_0 (1 - exp(-rho_s / rho_0)); a wall neighbour takes the centre value
+        for (int sp = 0; sp < 2; sp++) {
+          const double* rs = sp ? rb : rr;
+          const double pc = a.rho0 * (1.0 - exp(-rs[n] / a.rho0));
+          auto psi_at = [&](int dx, int dy, int dz) {
+            const long long m = nb_index(x, y, z, dx, dy, dz, a.nx, a.ny, a.nz);
+            return (solid && solid[m]) ? pc : a.rho0 * (1.0 - exp(-rs[m] / a.rho0));
+          };
+          double att[3] = {0.0, 0.0, 0.0}, rep[3] = {0.0, 0.0, 0.0};
+          for (int q = 0; q < L::NP; q++) {
+            const double d = L::w(L::pgrp(q)) * (psi_at(L::pcx(q), L::pcy(q), L::pcz(q)) -
+                                                 psi_at(-L::pcx(q), -L::pcy(q), -L::pcz(q)));
+            att[0] += L::pcx(q) * d;
+            att[1] += L::pcy(q) * d;
+            att[2] += L::pcz(q) * d;
+          }
+          for (int dz = 0; dz <= 2; dz++)
+            for (int dy = -2; dy <= 2; dy++)
+              for (int dx = -2; dx <= 2; dx++) {
+                const int r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 == 0 || mr_weight(r2) == 0.0 || !(dz > 0 || dy > 0 || (dy == 0 && dx > 0))) continue;
+                const double d = mr_weight(r2) * (psi_at(dx, dy, dz) - psi_at(-dx, -dy, -dz));
+                rep[0] += dx * d;
+                rep[1] += dy * d;
+                rep[2] += dz * d;
+              }
+          for (int dd = 0; dd < 3; dd++) F[dd] += -a.Ga[sp] * pc * att[dd] - a.Gr[sp] * pc * rep[dd];
+        }
       }
     }
     double u[3] = {0.0, 0.0, 0.0};

@@ -138,7 +138,8 @@ lbm_status lbm_batch_set(lbm_batch* b, lbm_ctx* const* ctxs, const int32_t* nste
     const lbm_ctx* c = ctxs[j];
     if (!c || nsteps[j] < 0) return LBM_EINVAL;
     if (c->sticky != LBM_OK || !c->initialised) return LBM_ESTATE;
-    if (c->p.precision != b->precision || c->has_walls || c->rep || c->aa || c->stream != b->stream)
+    if (c->p.precision != b->precision || c->has_walls || c->rep || c->aa || c->p.model == LBM_MODEL_SC_MR ||
+        c->stream != b->stream)
       return LBM_EINVAL;
     nunits += units_of(c);
   }

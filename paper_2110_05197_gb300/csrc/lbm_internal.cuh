@@ -139,10 +139,14 @@ StepParams<T> make_step_params(const lbm_ctx* c) {
   s.inv_rho_b0 = T(1.0 / q.rho_b0);
   s.enhanced = q.enhanced_eq;
   s.color_norm = q.color_norm;
-  if (q.model == LBM_MODEL_SC_2C)
+  if (q.model == LBM_MODEL_SC_2C || q.model == LBM_MODEL_SC_MR)
     s.G = T(q.G / (q.rho0_psi * q.rho0_psi));
   else
     s.G = T(q.G);
+  for (int k = 0; k < 2; k++) {
+    s.Ga[k] = T(q.Ga[k]);
+    s.Gr[k] = T(q.Gr[k]);
+  }
   s.rho0 = T(q.rho0_psi);
   s.inv_rho0 = T(1.0 / q.rho0_psi);
   s.omega_r = T(1.0 / q.tau_r);

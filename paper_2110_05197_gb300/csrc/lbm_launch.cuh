@@ -160,34 +160,41 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
   return cudaLaunchKernelEx(&cfg, kern, c->tma[c->cur], fout, rout, c->solid, &c->diag->status, sp);
 }
 
-// In-place (AA) step: the field pass, then the step kernel, both over all nodes.
+// Field-pass step (in-place streaming, or the multirange model): the field pass, then the
+// step kernel, both over all nodes.
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
-cudaError_t launch_aa_t(lbm_ctx* c) {
+cudaError_t launch_fp_t(lbm_ctx* c) {
   if constexpr (REP) {
     cudaError_t e = launch_rep_prepass_t<L, T, S, RT>(c, c->cur);
     if (e != cudaSuccess) return e;
   }
   const StepParams<T> sp = make_step_params<T>(c);
-  const int odd = c->cur & 1;
-  S* f = static_cast<S*>(c->f[0]);
-  RT* r = static_cast<RT*>(c->r[0]);
+  const int odd = c->aa ? (c->cur & 1) : 0;
+  const int mode = c->aa ? 1 + odd : 0;
+  const S* fin = static_cast<const S*>(c->f[c->cur]);
+  S* fout = static_cast<S*>(c->f[c->cur ^ 1]);  // == fin in place
+  const RT* rin = static_cast<const RT*>(c->r[c->cur]);
+  RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
   T* fld = reinterpret_cast<T*>(c->stage);  // [NF + K][N] of the compute type, fits 6N doubles
   const long long blocks = (c->N + 255) / 256;
   const int grid = (int)std::min<long long>(blocks, (long long)c->nsm * 16);
-  aa_fields_kernel<L, T, S, RT, MODEL><<<grid, 256, 0, c->stream>>>(f, r, fld, WALLS ? c->solid : nullptr,
+  fp_fields_kernel<L, T, S, RT, MODEL><<<grid, 256, 0, c->stream>>>(fin, rin, fld, WALLS ? c->solid : nullptr,
                                                                    &c->diag->status, sp, odd);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   c->launches += 1;
-  aa_step_kernel<L, T, S, RT, MODEL, WALLS, REP><<<grid, 256, 0, c->stream>>>(
-      f, r, fld, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour), static_cast<const T*>(c->normals),
-      rep_params(c), odd);
+  fp_step_kernel<L, T, S, RT, MODEL, WALLS, REP><<<grid, 256, 0, c->stream>>>(
+      fin, fout, rin, rout, fld, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour),
+      static_cast<const T*>(c->normals), rep_params(c), mode);
   return cudaGetLastError();
 }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 cudaError_t launch_step_t(lbm_ctx* c) {
-  if (c->aa) return launch_aa_t<L, T, S, RT, MODEL, WALLS, REP>(c);
+  if constexpr (MODEL == kSCMR) {
+    return launch_fp_t<L, T, S, RT, MODEL, WALLS, REP>(c);
+  } else {
+  if (c->aa) return launch_fp_t<L, T, S, RT, MODEL, WALLS, REP>(c);
   if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
     if (c->tma_ok && c->tx == kTmaTX && c->ty == 4 && c->p.nx / kTmaTX <= kMaxCluster &&
         (long long)c->K * c->Q * c->N < (1LL << 31))
@@ -236,6 +243,7 @@ cudaError_t launch_step_t(lbm_ctx* c) {
       fin, fout, rin, rout, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour),
       static_cast<const T*>(c->normals), rep_params(c));
   return cudaGetLastError();
+  }
 }
 
 template <class L, class T, class S, class RT, int MODEL>
@@ -249,14 +257,19 @@ cudaError_t dispatch_walls(lbm_ctx* c) {
 
 template <class T, class S, class RT, int MODEL>
 cudaError_t dispatch_lattice(lbm_ctx* c) {
-  if (c->p.lattice == LBM_D3Q19) return dispatch_walls<D3Q19, T, S, RT, MODEL>(c);
-  return dispatch_walls<D2Q9, T, S, RT, MODEL>(c);
+  if constexpr (MODEL == kSCMR) {
+    return dispatch_walls<D3Q19, T, S, RT, MODEL>(c);  // D3Q19 only (lbm_create checks)
+  } else {
+    if (c->p.lattice == LBM_D3Q19) return dispatch_walls<D3Q19, T, S, RT, MODEL>(c);
+    return dispatch_walls<D2Q9, T, S, RT, MODEL>(c);
+  }
 }
 
 template <class T, class S, class RT>
 cudaError_t dispatch_model(lbm_ctx* c) {
   if (c->p.model == LBM_MODEL_CG) return dispatch_lattice<T, S, RT, kCG>(c);
   if (c->p.model == LBM_MODEL_SC_MP) return dispatch_lattice<T, S, RT, kSCMP>(c);
+  if (c->p.model == LBM_MODEL_SC_MR) return dispatch_lattice<T, S, RT, kSCMR>(c);
   return dispatch_lattice<T, S, RT, kSC2C>(c);
 }
 

@@ -42,7 +42,7 @@
 
 namespace lbm {
 
-enum Model : int { kCG = 0, kSCMP = 1, kSC2C = 2 };
+enum Model : int { kCG = 0, kSCMP = 1, kSC2C = 2, kSCMR = 3 };
 
 // Step parameters, converted to the compute type on the host.
 template <class T>
@@ -60,6 +60,7 @@ struct StepParams {
   int enhanced, color_norm;
   // SC
   T G, rho0, inv_rho0;    // multiphase: G, rho_0; two-component: G_eff = G/rho0^2 in G
+  T Ga[2], Gr[2];         // multirange: attractive / repulsive self-couplings per species
   T omega_r, omega_b;     // 1/tau_k (SC)
   // forces
   T body[3];
@@ -82,6 +83,11 @@ template <>
 struct ModelTraits<kSC2C> {
   static constexpr int K = 2;
   static constexpr int NF = 2;  // rho_1, rho_2
+};
+template <>
+struct ModelTraits<kSCMR> {
+  static constexpr int K = 2;
+  static constexpr int NF = 4;  // rho_1, rho_2, Psi_1, Psi_2
 };
 
 // ---- storage conversions ----
@@ -161,6 +167,11 @@ __device__ __forceinline__ void node_fields(const StepParams<T>& p, T s0, T s1, 
     }
   } else if constexpr (MODEL == kSCMP) {
     out[0] = p.rho0 * (T(1) - fexp(-s0 * p.inv_rho0));  // Eq. pseudopotential
+  } else if constexpr (MODEL == kSCMR) {
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = p.rho0 * (T(1) - fexp(-s0 * p.inv_rho0));  // Psi_s, Eq. pseudopotential per species
+    out[3] = p.rho0 * (T(1) - fexp(-s1 * p.inv_rho0));
   } else {
     out[0] = s0;
     out[1] = s1;
@@ -443,6 +454,77 @@ __device__ __forceinline__ void sc2c_collide(const StepParams<T>& p, T (&g)[2][L
   for (int a = 0; a < 3; a++) u[a] = (j1[a] + j2[a] + T(0.5) * (F1[a] + F2[a])) * inv;
   bgk_guo<L, T>(p, g[0], c1, u, F1, p.omega_r);
   bgk_guo<L, T>(p, g[1], c2, u, F2, p.omega_b);
+}
+
+// Forcing weight p of a belt vector with |c|^2 = r2 (Eq. pweights).
+__host__ __device__ constexpr double mr_weight(int r2) {
+  return r2 == 1 ? 4.0 / 135.0
+       : r2 == 2 ? 1.0 / 63.0
+       : r2 == 3 ? 2.0 / 315.0
+       : r2 == 4 ? 5.0 / 1512.0
+       : r2 == 5 ? 1.0 / 945.0
+       : r2 == 6 ? 1.0 / 1890.0
+       : r2 == 8 ? 1.0 / 15120.0
+                 : 0.0;
+}
+
+// sum_j p_j phi(x + e_j) e_j over belts 1 and 2 (the 92 non-zero integer vectors with
+// |e|^2 <= 8), as 46 opposite-pair differences; far(fi, dx, dy, dz) reads the field fi.
+template <class T, class FAR>
+__device__ __forceinline__ void belt_sum(const FAR& far, int fi, T (&acc)[3]) {
+  acc[0] = acc[1] = acc[2] = T(0);
+#pragma unroll
+  for (int dz = 0; dz <= 2; dz++)
+#pragma unroll
+    for (int dy = -2; dy <= 2; dy++)
+#pragma unroll
+      for (int dx = -2; dx <= 2; dx++) {
+        const int r2 = dx * dx + dy * dy + dz * dz;
+        const bool positive = dz > 0 || (dy > 0 || (dy == 0 && dx > 0));  // one of each pair
+        if (r2 == 0 || r2 > 8 || mr_weight(r2) == 0.0 || !positive) continue;
+        const T d = T(mr_weight(r2)) * (far(fi, dx, dy, dz) - far(fi, -dx, -dy, -dz));
+        if (dx) acc[0] += T(dx) * d;
+        if (dy) acc[1] += T(dy) * d;
+        if (dz) acc[2] += T(dz) * d;
+      }
+}
+
+// Multicomponent SC with multirange potentials (Eq. benziforces): per species s the
+// attractive belt-1 force -G^a_s Psi_s sum_i w_i Psi_s(x+c_i) c_i (Eq.
+// doublebeltattractiveforce), the repulsive belts-1+2 force -G^r_s Psi_s sum_j p_j
+// Psi_s(x+e_j) e_j (Eq. doublebeltrepulsionforce) and the cross force of Eq.
+// doublebeltrepulsionforce2; then BGK + Guo with the common velocity as sc2c_collide.
+// Fields: 0 rho_1, 1 rho_2, 2 Psi_1, 3 Psi_2; nbr(fi, i) at the lattice neighbours,
+// far(fi, dx, dy, dz) at any offset up to 2.
+template <class L, class T, class NB, class FAR>
+__device__ __forceinline__ void scmr_collide(const StepParams<T>& p, T (&g)[2][L::Q], const CompState<T>& c1,
+                                             const CompState<T>& c2, const NB& nbr, const FAR& far) {
+  const T r1 = c1.rho, r2 = c2.rho;
+  const T rho = r1 + r2;
+  const T inv = frcp(rho);
+  T F[2][3];
+#pragma unroll
+  for (int s = 0; s < 2; s++) {
+    T att[3], rep[3], crs[3];
+    weighted_sum<L, T>(nbr, 2 + s, att);  // belt 1, w: Psi_s
+    belt_sum<T>(far, 2 + s, rep);         // belts 1 + 2, p: Psi_s
+    weighted_sum<L, T>(nbr, 1 - s, crs);  // belt 1, w: rho of the other species
+    const T psic = nbr(2 + s, 0);
+    const T rs = s == 0 ? r1 : r2;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const T b = p.has_body ? p.body[a] : T(0);
+      F[s][a] = -p.Ga[s] * psic * att[a] - p.Gr[s] * psic * rep[a] - p.G * rs * crs[a] + b * rs * inv;
+    }
+  }
+  T j1[3], j2[3];
+  momentum<L, T>(g[0], j1);
+  momentum<L, T>(g[1], j2);
+  T u[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) u[a] = (j1[a] + j2[a] + T(0.5) * (F[0][a] + F[1][a])) * inv;
+  bgk_guo<L, T>(p, g[0], c1, u, F[0], p.omega_r);
+  bgk_guo<L, T>(p, g[1], c2, u, F[1], p.omega_b);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -1,4 +1,5 @@
-// In-place streaming (AA pattern): one population buffer instead of two.
+// Field-pass steps: in-place streaming (AA pattern) with one population buffer, and the
+// multirange Shan-Chen model, whose repulsive force reaches distance 2.
 //
 // Storage.  After an even number of steps the canonical population f^k_i(x) sits in slot i
 // of node x; after an odd number, in slot opp(i) of node x - c_i.  An even step reads the
@@ -19,6 +20,11 @@
 // and the step kernel reads its neighbours' values from there: 2*K*Q populations plus
 // K*Q more per node for the pass, i.e. 1.5x the bytes of a two-buffer step, for half the
 // population memory.
+//
+// The multirange SC model (Eq. benziforces) needs Psi at distance 2, beyond the halo of the
+// plane-marching kernels, so it runs on the same two kernels in either storage mode: the
+// field pass stores rho_s, Psi_s and q_s of every node, the step kernel reads the 92
+// neighbours of belts 1 and 2 from there (L1/L2 serve the re-reads).
 #pragma once
 
 #include "lbm_step.cuh"
@@ -45,7 +51,7 @@ __device__ __forceinline__ long long aa_index_n(int k, int i, long long n, int n
 // Field pass: fld[NF + K][N] = the stencil fields (node_fields) and the new reference
 // densities q_k of every fluid node, from the state at t (layout parity `odd`).
 template <class L, class T, class S, class RT, int MODEL>
-__global__ void __launch_bounds__(256) aa_fields_kernel(const S* __restrict__ f, const RT* __restrict__ r,
+__global__ void __launch_bounds__(256) fp_fields_kernel(const S* __restrict__ f, const RT* __restrict__ r,
                                                         T* __restrict__ fld, const uint8_t* __restrict__ solid,
                                                         const int* __restrict__ status, const StepParams<T> p,
                                                         int odd) {
@@ -65,22 +71,25 @@ __global__ void __launch_bounds__(256) aa_fields_kernel(const S* __restrict__ f,
       rho[k] = c.rho;
       fld[(long long)(NF + k) * N + n] = c.q;
     }
-    T out[2];
+    T out[NF > 2 ? NF : 2];
     node_fields<MODEL, T>(p, rho[0], rho[1], out);
 #pragma unroll
     for (int fi = 0; fi < NF; fi++) fld[(long long)fi * N + n] = out[fi];
   }
 }
 
-// One in-place step (layout parity `odd` at t), one thread per node: moments, stencil from
-// the field pass, collision (the same per-node code as the two-buffer kernels), streaming.
+// One step, one thread per node: moments, stencil from the field pass, collision (the same
+// per-node code as the plane-marching kernels), streaming.  mode 0: two buffers (read fin,
+// rin; push into fout, rout); mode 1 / 2: in place at even / odd layout parity (fin == fout,
+// rin == rout; the pointers may alias, so none is restrict-qualified).
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
 __global__ void __launch_bounds__(256, min_blocks<T>())
-    aa_step_kernel(S* __restrict__ f, RT* __restrict__ r, const T* __restrict__ fld,
+    fp_step_kernel(const S* fin, S* fout, const RT* rin, RT* rout, const T* __restrict__ fld,
                    const uint8_t* __restrict__ solid, const int* __restrict__ status,
                    const __grid_constant__ StepParams<T> p, const T* __restrict__ colour,
-                   const T* __restrict__ normals, const __grid_constant__ RepParams rp, int odd) {
+                   const T* __restrict__ normals, const __grid_constant__ RepParams rp, int mode) {
   if (*status != 0) return;
+  const bool inplace = mode != 0, odd = mode == 2;
   constexpr int Q = L::Q, K = ModelTraits<MODEL>::K, NF = ModelTraits<MODEL>::NF;
   const long long N = p.n;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
@@ -104,9 +113,9 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
       for (int i = 0; i < Q; i++) {
         const long long src = (odd && i != 0) ? (long long)(k * Q + opp<L>(i)) * N + nb(opp<L>(i))
                                               : (long long)(k * Q + i) * N + n;
-        g[k][i] = ld_s<S, T>(f[src]);
+        g[k][i] = ld_s<S, T>(fin[src]);
       }
-      cs[k] = comp_state<L, T, RT>(g[k], T(r[(long long)k * N + n]));
+      cs[k] = comp_state<L, T, RT>(g[k], T(rin[(long long)k * N + n]));
     }
     auto nbr = [&](int fi, int i) -> T {
       const long long m = nb(i);
@@ -117,13 +126,20 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
       T Fx[3] = {T(0), T(0), T(0)};
       if constexpr (REP) rep_force<L, T>(normals, colour, WALLS ? solid : nullptr, x, y, z, rp, Fx);
       cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
+    } else if constexpr (MODEL == kSCMR) {
+      auto far = [&](int fi, int dx, int dy, int dz) -> T {
+        const long long m = wrap_index(x + dx, y + dy, z + dz, p.nx, p.ny, p.nz);
+        if (WALLS && solid[m]) return fld[(long long)fi * N + n];
+        return fld[(long long)fi * N + m];
+      };
+      scmr_collide<L, T>(p, g, cs[0], cs[1], nbr, far);
     } else if constexpr (MODEL == kSCMP) {
       scmp_collide<L, T>(p, g, cs[0], nbr);
     } else {
       sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
     }
 #pragma unroll
-    for (int k = 0; k < K; k++) r[(long long)k * N + n] = RT(cs[k].q);
+    for (int k = 0; k < K; k++) rout[(long long)k * N + n] = RT(cs[k].q);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
       const long long d = nb(i);
@@ -135,11 +151,11 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
         long long dst;
         if (i == 0)
           dst = (long long)(k * Q) * N + n;
-        else if (!odd)
-          dst = bounce ? (long long)(k * Q + i) * N + d : (long long)(k * Q + opp<L>(i)) * N + n;
-        else
+        else if (!inplace || odd)  // push to x + c_i; bounce-back into opp(i) of x
           dst = bounce ? (long long)(k * Q + opp<L>(i)) * N + n : (long long)(k * Q + i) * N + d;
-        f[dst] = st_s<S, T>(v);
+        else                       // even in-place step: back into opp(i) of x
+          dst = bounce ? (long long)(k * Q + i) * N + d : (long long)(k * Q + opp<L>(i)) * N + n;
+        fout[dst] = st_s<S, T>(v);
       }
     }
   }

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 D2Q9, D3Q19 = 0, 1
-CG, SC_MP, SC_2C = 0, 1, 2
+CG, SC_MP, SC_2C, SC_MR = 0, 1, 2, 3
 FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 STREAM_AB, STREAM_AA = 0, 1
 NTOTALS = 10
@@ -49,6 +49,7 @@ class _CParams(ctypes.Structure):
         ("diag_every", ctypes.c_int32),
         ("umax_unstable", ctypes.c_double),
         ("streaming", ctypes.c_int32),
+        ("Ga", ctypes.c_double * 2), ("Gr", ctypes.c_double * 2),
     ]
 
 
@@ -158,13 +159,15 @@ class Params:
     diag_every: int = 0
     umax_unstable: float = 0.5
     streaming: int = 0          # STREAM_AB (two buffers) or STREAM_AA (in place)
+    Ga: tuple = (0.0, 0.0)      # SC_MR: attractive self-couplings per species
+    Gr: tuple = (0.0, 0.0)      # SC_MR: repulsive self-couplings per species
 
     def to_c(self) -> _CParams:
         p = _CParams()
         for f in fields(self):
             v = getattr(self, f.name)
-            if f.name == "body_force":
-                p.body_force = (ctypes.c_double * 3)(*[float(x) for x in v])
+            if f.name in ("body_force", "Ga", "Gr"):
+                setattr(p, f.name, (ctypes.c_double * len(v))(*[float(x) for x in v]))
             else:
                 setattr(p, f.name, v)
         return p

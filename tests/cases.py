@@ -75,6 +75,26 @@ def sc_walls2d(nx=24, ny=20, **extra):
     return Case("sc_walls2d", kw, rho, None, None, solid)
 
 
+def sc_mr3d(nx=14, ny=12, nz=11, seed=7, walls=False, **extra):
+    """Multicomponent SC with multirange potentials (Eq. benziforces): a drop of species A
+    (1.18 with 0.18 of B, Table dropcolParams set 1) in B, the printed self-couplings
+    G^a = (-9, -8), G^r = (8.1, 7.1), rho_0 = 0.83, and the cross coupling G_AB = 1.215
+    (three times the printed 0.405, which with these lattice weights does not demix)."""
+    n = nx * ny * nz
+    ins = inputs.ellipsoid(nx, ny, nz, (4.5, 3.8, 3.4))
+    rr = np.where(ins, 1.18, 0.18) * (1 + 0.01 * inputs.uniform_pm1(seed, n, 0))
+    rb = np.where(ins, 0.18, 1.18) * (1 + 0.01 * inputs.uniform_pm1(seed, n, 1))
+    kw = dict(lattice=1, model=3, nx=nx, ny=ny, nz=nz, Ga=(-9.0, -8.0), Gr=(8.1, 7.1), G=1.215, rho0_psi=0.83,
+              tau_r=1.0, tau_b=0.9)
+    solid = None
+    if walls:
+        solid = inputs.channel_walls(nx, ny, nz)
+        rr, rb = np.where(solid, 0.0, rr), np.where(solid, 0.0, rb)
+        kw["body_force"] = (1e-5, 0.0, 2e-6)
+    kw.update(extra)
+    return Case("sc_mr3d", kw, rr, rb, None, solid)
+
+
 def cg_rep3d(nx=30, ny=16, nz=15, seed=6, **extra):
     """Two droplets about two nodes apart, with different radii and offset centres so that
     the normals in the gap are generic (no symmetry puts a Heaviside argument at FP32
@@ -116,6 +136,8 @@ SMALL_CASES = {
     "sc_mp3d": sc_mp3d,
     "sc_2c3d": sc_2c3d,
     "sc_walls2d": sc_walls2d,
+    "sc_mr3d": sc_mr3d,
+    "sc_mr_walls": lambda: sc_mr3d(nx=13, ny=12, nz=10, walls=True),
     "cg_rep3d": cg_rep3d,
     "cg_rep_film": cg_rep_film,
     # the printed psi_rep = (1 + |rho^N|)^chi is largest where |grad rho^N| is near zero and

@@ -75,6 +75,7 @@ def test_workspace_size_query(L):
     dict(rho_b0=-1.0), dict(model=lbm.SC_MP, rho0_psi=0.0), dict(diag_every=-1),
     dict(rho_r0=0.1, rho_b0=1.0),  # alpha_R < 0 from Eq. gamma
     dict(streaming=2),
+    dict(model=lbm.SC_MR, lattice=lbm.D2Q9, nz=1), dict(model=4),
 ])
 def test_invalid_parameters_rejected(L, bad):
     rc, _ = _size(L, **bad)
