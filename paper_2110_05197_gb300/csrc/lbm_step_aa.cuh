@@ -161,4 +161,127 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
   }
 }
 
+// The same step for D3Q19 with the neighbours' fields staged in shared memory (used for the
+// multirange model): a block of
+// TX x TY = 32 x 8 threads takes work units (column tile, z-chunk) as the plane-marching
+// kernels do and marches z; a ring of 2H+1 planes holds the fields (and wall mask) of the
+// (TX+2H) x (TY+2H) extended tile, H = 2 for the multirange model (belt 2) and 1 otherwise,
+// loaded with coalesced rows from the field pass's array.  Populations move as in
+// fp_step_kernel (mode 0 two buffers, 1 / 2 in place at even / odd parity).
+constexpr int kFpTX = 32, kFpTY = 8;
+
+template <class T, int MODEL, bool WALLS, int H>
+__host__ __device__ constexpr size_t fpt_smem_bytes() {
+  constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
+  constexpr size_t ne = size_t(kFpTX + 2 * H) * (kFpTY + 2 * H);
+  return (((2 * H + 1) * (NV * ne * sizeof(T) + (WALLS ? ne : 0))) + 15) & ~size_t(15);
+}
+
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, int H>
+__global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
+    fpt_step_kernel(const S* fin, S* fout, const RT* rin, RT* rout, const T* __restrict__ fld,
+                    const uint8_t* __restrict__ solid, const int* __restrict__ status,
+                    const __grid_constant__ StepParams<T> p, const T* __restrict__ colour,
+                    const T* __restrict__ normals, const __grid_constant__ RepParams rp, int mode) {
+  if (*status != 0) return;
+  static_assert(L::D == 3, "plane marching");
+  constexpr int TX = kFpTX, TY = kFpTY;
+  constexpr int EX = TX + 2 * H, NE = EX * (TY + 2 * H), NS = 2 * H + 1;
+  constexpr int Q = L::Q, K = ModelTraits<MODEL>::K, NF = ModelTraits<MODEL>::NF, NV = NF + K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sf = reinterpret_cast<T*>(smem_raw);                      // [NS][NV][NE]
+  uint8_t* sm = reinterpret_cast<uint8_t*>(sf + NS * NV * NE);  // [NS][NE] (walls)
+  const bool inplace = mode != 0, odd = mode == 2;
+  const long long N = p.n;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  auto slot = [](int z) { return ((z % NS) + NS) % NS; };
+  WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
+  Segment sg;
+  while (work.pop(sg)) {
+    const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
+    auto load = [&](int z) {
+      const int sl = slot(z);
+      const int gz = wrap(z, p.nz);
+      for (int e = tid; e < NE; e += TX * TY) {
+        const int ey = e / EX, ex = e - ey * EX;
+        const long long m = wrap(x0 - H + ex, p.nx) + (long long)p.nx * (wrap(y0 - H + ey, p.ny) + (long long)p.ny * gz);
+#pragma unroll
+        for (int fi = 0; fi < NV; fi++) sf[(sl * NV + fi) * NE + e] = fld[(long long)fi * N + m];
+        if (WALLS) sm[sl * NE + e] = solid[m];
+      }
+    };
+    for (int z = sg.z0 - H; z < sg.z0 + H; z++) load(z);
+    for (int z = sg.z0; z < sg.z1; z++) {
+      load(z + H);
+      __syncthreads();
+      const int x = x0 + tx, y = y0 + ty;
+      const int e0 = (ty + H) * EX + (tx + H);
+      const int sl0 = slot(z);
+      if (x < p.nx && y < p.ny && !(WALLS && sm[sl0 * NE + e0])) {
+        const long long n = x + (long long)p.nx * (y + (long long)p.ny * z);
+        const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x + 1 >= p.nx ? 0 : x + 1;
+        const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y + 1 >= p.ny ? 0 : y + 1;
+        const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z + 1 >= p.nz ? 0 : z + 1;
+        auto nb = [&](int i) -> long long {
+          const int X = cx<L>(i) == 0 ? x : (cx<L>(i) > 0 ? xp : xm);
+          const int Y = cy<L>(i) == 0 ? y : (cy<L>(i) > 0 ? yp : ym);
+          const int Z = cz<L>(i) == 0 ? z : (cz<L>(i) > 0 ? zp : zm);
+          return X + (long long)p.nx * (Y + (long long)p.ny * Z);
+        };
+        T g[K][Q];
+        CompState<T> cs[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+#pragma unroll
+          for (int i = 0; i < Q; i++) {
+            const long long src = (odd && i != 0) ? (long long)(k * Q + opp<L>(i)) * N + nb(opp<L>(i))
+                                                  : (long long)(k * Q + i) * N + n;
+            g[k][i] = ld_s<S, T>(fin[src]);
+          }
+          cs[k] = comp_state<L, T, RT>(g[k], T(rin[(long long)k * N + n]));
+        }
+        auto at = [&](int fi, int dx, int dy, int dz) -> T {
+          const int sl = slot(z + dz), e = e0 + dy * EX + dx;
+          if (WALLS && sm[sl * NE + e]) return sf[(sl0 * NV + fi) * NE + e0];
+          return sf[(sl * NV + fi) * NE + e];
+        };
+        auto nbr = [&](int fi, int i) -> T { return at(fi, cx<L>(i), cy<L>(i), cz<L>(i)); };
+        if constexpr (MODEL == kCG) {
+          T Fx[3] = {T(0), T(0), T(0)};
+          if constexpr (REP) rep_force<L, T>(normals, colour, WALLS ? solid : nullptr, x, y, z, rp, Fx);
+          cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
+        } else if constexpr (MODEL == kSCMR) {
+          scmr_collide<L, T>(p, g, cs[0], cs[1], nbr, at);
+        } else if constexpr (MODEL == kSCMP) {
+          scmp_collide<L, T>(p, g, cs[0], nbr);
+        } else {
+          sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) rout[(long long)k * N + n] = RT(cs[k].q);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+          const long long d = nb(i);
+          const int sl = slot(z + cz<L>(i)), ed = e0 + cy<L>(i) * EX + cx<L>(i);
+          const bool bounce = WALLS && i != 0 && sm[sl * NE + ed];
+#pragma unroll
+          for (int k = 0; k < K; k++) {
+            T v = g[k][i];
+            if (i != 0 && !bounce) v += p.phi[k][grp<L>(i)] * (cs[k].q - sf[(sl * NV + NF + k) * NE + ed]);
+            long long dst;
+            if (i == 0)
+              dst = (long long)(k * Q) * N + n;
+            else if (!inplace || odd)
+              dst = bounce ? (long long)(k * Q + opp<L>(i)) * N + n : (long long)(k * Q + i) * N + d;
+            else
+              dst = bounce ? (long long)(k * Q + i) * N + d : (long long)(k * Q + opp<L>(i)) * N + n;
+            fout[dst] = st_s<S, T>(v);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace lbm
