@@ -39,6 +39,10 @@
  *   - Walls: halfway bounce-back; a solid neighbour's scalar is replaced by the centre's.
  *   - psi_rep defaults to (1-|rho^N|)^chi (maximal at rho^N = 0, decaying away from it);
  *     H(0) = 0; direction 0 is skipped; a node or neighbour with |grad rho^N| <= eps adds 0.
+ *   - Repulsion sign: the printed sum of Eq. repForce points, at the two nodes flanking a
+ *     rho^N extremum, toward the extremum (for either orientation of the normals, the
+ *     terms are quadratic in them), which squeezes the film between two interfaces and
+ *     drains it; the text calls the force outward (repulsive), so F_rep is minus that sum.
  *   - Two-component SC: common barycentric velocity, each species relaxes with its own tau.
  *   - D2Q9 constants (the paper prints D3Q19 only) are chosen to satisfy the same moment
  *     identities as the D3Q19 set.
@@ -374,7 +378,9 @@ static void repulsion_at(const orc_sim* s, size_t n, double* Fr) {
     double cl = cnorm(&s->L, i);
     for (int d = 0; d < 3; d++) acc[d] += H * (nc * nrm[d] / cl + n2c * n2[d] / cl);
   }
-  for (int d = 0; d < 3; d++) Fr[d] = s->p.rep_pi * psi_rep * acc[d];
+  /* outward: the sum points from the film's edge nodes toward the rho^N extremum between
+     two interfaces; the force is the repulsive (outward) one of Sec. 2.3, its negative */
+  for (int d = 0; d < 3; d++) Fr[d] = -s->p.rep_pi * psi_rep * acc[d];
 }
 
 static void stage_cg_force(orc_sim* s) {

@@ -90,7 +90,8 @@ __device__ __forceinline__ void rep_force(const T* __restrict__ normals, const T
   }
   const T c = colour[m];
   const T base = a.psi_kind ? T(1) + fabs(c) : T(1) - fabs(c);
-  const T s = T(a.pi) * fpow<T>(base, T(a.chi));
+  // outward (repulsive, Sec. 2.3): the printed sum points toward the rho^N extremum
+  const T s = -T(a.pi) * fpow<T>(base, T(a.chi));
   for (int d = 0; d < 3; d++) F[d] = s * acc[d];
 }
 

@@ -150,7 +150,7 @@ class BruteForce:
             H = (-(nc * n2c) > 0) & ok2
             acc += np.where(H, (nc * n + n2c * n2) / L.norm[i], 0.0)
         base = 1 + np.abs(rhoN) if p.rep_printed else 1 - np.abs(rhoN)
-        F = p.rep_pi * base ** p.rep_chi * acc
+        F = -p.rep_pi * base ** p.rep_chi * acc   # outward: away from the rho^N extremum
         return np.where(ok & self.fluid, F, 0.0)
 
     # ---- equilibria and operators ----

@@ -336,8 +336,9 @@ def test_repulsion_only_at_colour_extrema(orc):
 def test_repulsion_in_thin_film(orc):
     """Two red slabs separated by a 4-node blue film centred at x = 20.5 (mirror-symmetric
     box): the two film nodes next to the rho^N minimum have opposite normals across their
-    link, so F_rep acts there only, equal and opposite, pointing toward the film centre
-    (raising the film's pressure against drainage); its total is zero."""
+    link, so F_rep acts there only, equal and opposite, pointing away from the film centre
+    toward the interfaces (outward, Sec. 2.3: it raises the pressure against the
+    interfaces and pushes them apart); its total is zero."""
     n = 41
     x = np.arange(n)
     film = (x >= 19) & (x < 23)
@@ -349,7 +350,7 @@ def test_repulsion_in_thin_film(orc):
     F = s.force()[0].reshape(4, 4, n)[0, 0]
     nzx = np.nonzero(F)[0]
     assert set(nzx.tolist()) == {20, 21}
-    assert F[20] > 1e-4 and abs(F[20] + F[21]) < 1e-15
+    assert F[20] < -1e-4 and abs(F[20] + F[21]) < 1e-15
     Fall = s.force()
     assert np.max(np.abs(Fall[1:])) == 0.0
 
