@@ -29,6 +29,8 @@ def shape_key(lat: "lbm.Lattice"):
 
 
 def candidates_for(p: "lbm.Params"):
+    if p.streaming == lbm.STREAM_AA or p.model == lbm.SC_MR:
+        return [(32, 8, 0)]  # the field-pass kernels choose their own launch shape
     cands = CANDIDATES_3D if p.lattice == lbm.D3Q19 else CANDIDATES_2D
     out = []
     for tx, ty, tz in cands:
