@@ -9,9 +9,12 @@ Two servers answer the same request trace:
   batch table have room, keeps their lattices resident, and advances all of them together:
   lattices up to ``batch_max_nodes`` nodes share one persistent batched launch per step
   (lbm_batch_*, replayed as a CUDA graph per tick of ``tick`` steps), larger ones are
-  stepped with their own tuned kernel on a second stream so their work overlaps the batch.
-  A finished request's moments are read and its memory is released at the end of the
-  tick in which it completes; new requests join at the next tick.
+  stepped with their own tuned kernel on a second stream so their work overlaps the batch,
+  first come first served (they share that stream, and interleaving them would only make
+  each finish later).  The two streams run independently: an event marks each one's work
+  in flight, and the host launches the next tick or job as soon as one completes.
+  A finished request's moments are read and its memory is released as soon as its work
+  completes; new small requests join at the next tick.
 
 Results are the FP64 totals (lbm_moments) and the component densities; the latency of a
 request is completion minus arrival on a common wall clock.  The physics of a job does
@@ -175,12 +178,23 @@ class BatchServer:
         t0 = time.perf_counter() if t0 is None else t0
         clock = lambda: time.perf_counter() - t0
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        active = []          # dicts: req, lat, left, start, bytes, small
+        smalls, bigs = [], []  # active jobs (dicts: req, lat, left, start, bytes, small, units)
         out = []
         used = 0
         units_used = 0
         dirty = False
-        while pending or active:
+        # each stream runs independently: an event marks the end of its work in flight
+        small_ev, small_running = None, []
+        big_ev, big_running = None, None
+
+        def finish(a):
+            nonlocal used, units_used
+            out.append(_finish(a["lat"], a["req"], a["start"], clock, self.keep_fields))
+            a["lat"].close()
+            used -= a["bytes"]
+            units_used -= a["units"]
+
+        while pending or smalls or bigs:
             now = clock()
             # admission: arrived requests, FIFO, while memory and table room remain
             while pending and pending[0].arrival <= now:
@@ -193,46 +207,60 @@ class BatchServer:
                     nx, ny, nz = req.grid
                     nu = math.ceil(nx / 32) * math.ceil(ny / 8) * (math.ceil(nz / 16) if nz > 1 else 1)
                 if used + need > self.budget or (small and (units_used + nu > self.max_units or
-                                                            sum(a["small"] for a in active) >= self.max_jobs)):
+                                                            len(smalls) >= self.max_jobs)):
                     break
                 pending.popleft()
                 lat = _new_lattice(req, self.precision, small_stream if small else big_stream, tuned=not small)
-                active.append(dict(req=req, lat=lat, left=req.steps, start=now, bytes=need, small=small, units=nu))
+                job = dict(req=req, lat=lat, left=req.steps, start=now, bytes=need, small=small, units=nu)
+                (smalls if small else bigs).append(job)
                 used += need
                 units_used += nu
                 dirty = dirty or small
             self.peak_bytes = max(self.peak_bytes, used)
-            self.peak_jobs = max(self.peak_jobs, len(active))
-            if not active:
-                if pending:
-                    time.sleep(min(1e-3, max(0.0, pending[0].arrival - clock())))
-                continue
-            smalls = [a for a in active if a["small"]]
-            if dirty:
-                batch.set([a["lat"] for a in smalls], [a["left"] for a in smalls])
-                dirty = False
-            if smalls:
-                batch.step(self.tick, graph=self.graph)
-            for a in active:
-                if not a["small"]:
-                    n = min(self.tick, a["left"])
+            self.peak_jobs = max(self.peak_jobs, len(smalls) + len(bigs))
+            progressed = False
+            # small lattices: one batched launch per step, ticks of `tick` steps as a graph;
+            # the job list changes only between ticks
+            if small_ev is None or small_ev.query():
+                if small_ev is not None:
+                    for a in small_running:
+                        a["left"] -= min(self.tick, a["left"])
+                        if a["left"] == 0:
+                            smalls.remove(a)
+                            finish(a)
+                            dirty = True
+                    small_ev, small_running = None, []
+                    progressed = True
+                if smalls:
+                    if dirty:
+                        batch.set([a["lat"] for a in smalls], [a["left"] for a in smalls])
+                        dirty = False
+                    batch.step(self.tick, graph=self.graph)
+                    small_ev = torch.cuda.Event()
+                    small_ev.record(small_stream)
+                    small_running = list(smalls)
+            # large lattices share the second stream, first come first served: the oldest
+            # runs all its steps (interleaving them would only make each finish later)
+            if big_ev is None or big_ev.query():
+                if big_ev is not None:
+                    bigs.remove(big_running)
+                    finish(big_running)
+                    big_ev, big_running = None, None
+                    progressed = True
+                if bigs:
+                    a = bigs[0]
                     l0 = a["lat"].launch_count()
-                    a["lat"].step(n)
+                    a["lat"].step(a["left"])
                     self.launches += a["lat"].launch_count() - l0
-            small_stream.synchronize()
-            big_stream.synchronize()
-            keep = []
-            for a in active:
-                a["left"] -= min(self.tick, a["left"])
-                if a["left"] == 0:
-                    out.append(_finish(a["lat"], a["req"], a["start"], clock, self.keep_fields))
-                    a["lat"].close()
-                    used -= a["bytes"]
-                    units_used -= a["units"]
-                    dirty = dirty or a["small"]
+                    a["left"] = 0
+                    big_ev = torch.cuda.Event()
+                    big_ev.record(big_stream)
+                    big_running = a
+            if not progressed:
+                if small_ev is None and big_ev is None and pending:
+                    time.sleep(min(1e-3, max(0.0, pending[0].arrival - clock())))
                 else:
-                    keep.append(a)
-            active = keep
+                    time.sleep(2e-5)
         self.launches += batch.launch_count()
         batch.close()
         return out

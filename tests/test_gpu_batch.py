@@ -90,7 +90,8 @@ def test_serving_batch_matches_plain(lbm):
     reqs = serve.sweep(10, seed=7, steps=(40, 120), rate_hz=200.0,
                        grids=[(64, 64, 1), (32, 32, 32), (24, 24, 24), (48, 32, 16)])
     plain = {r.rid: r for r in serve.PlainServer(lbm.FP32, keep_fields=True).run(reqs)}
-    batch = {r.rid: r for r in serve.BatchServer(lbm.FP16, budget_bytes=64 << 20, tick=16,
+    # 32^3 and 48 x 32 x 16 go to the large-lattice path (own kernel, second stream)
+    batch = {r.rid: r for r in serve.BatchServer(lbm.FP16, budget_bytes=64 << 20, tick=16, batch_max_nodes=20_000,
                                                  keep_fields=True).run(reqs)}
     assert set(plain) == set(batch) == {r.rid for r in reqs}
     for r in reqs:
