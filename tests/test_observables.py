@@ -48,3 +48,19 @@ def test_components_join_across_periodic_faces():
     rr = np.where(m, 1.0, 0.0).ravel()
     rb = np.where(m, 0.0, 1.0).ravel()
     assert obs.droplet_masses(rr, rb, shape) == [16.0, 2.0]
+
+
+def test_endpoint_along_z_of_a_capsule():
+    nx = ny = 16
+    nz = 64
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cx = cy = (nx - 1) / 2
+    cz = (nz - 1) / 2
+    half = 12.0                     # cylinder half-length; caps of radius 4 beyond it
+    dz = np.clip(np.abs(z - cz) - half, 0.0, None)
+    d = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + dz ** 2)
+    col = np.tanh((4.0 - d) / 2.0).ravel()
+    rr, rb = (1 + col) / 2, (1 - col) / 2
+    # the z line through (nx // 2, ny // 2) sits 0.5 off the axis in x and y
+    tip = half + np.sqrt(4.0 ** 2 - 2 * 0.5 ** 2)
+    assert abs(obs.endpoint_along_z(rr, rb, (nz, ny, nx)) - tip) < 0.05
