@@ -174,7 +174,8 @@ const char* lbm_status_string(lbm_status s);
  * D3Q19 lattices in FP32/FP16/BF16 with nx % 32 == 0 and ny % 8 == 0 run the TMA-staged
  * kernel when tx x ty is 32 x 8 (for nx <= 256 as clusters of nx / 32 blocks that exchange
  * the x-halo in distributed shared memory; the cluster kernel also takes 32 x 4, with two
- * blocks per SM), the generic kernel otherwise.  Results are
+ * blocks per SM, and 64 x 4 when nx % 64 == 0, in clusters of nx / 64), the generic kernel
+ * otherwise.  Results are
  * bitwise independent of the shape within each kernel; the kernels agree to a few ulps of
  * the stored populations (the compiler fuses multiply-adds differently).  LBM_EINVAL for
  * shapes outside those limits. */

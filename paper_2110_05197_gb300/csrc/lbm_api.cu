@@ -195,6 +195,13 @@ bool build_tma_maps(lbm_ctx* c) {
               encode4(fn, &m.pop_main_mid4, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, kTmaTX, 4) &&
               encode4(fn, &m.ref_main_mid4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
                       c->N, kTmaTX, 4);
+    if (ok && p.nx % 64 == 0)
+      ok = encode4(fn, &m.pop_w_row, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, 64, 1) &&
+           encode4(fn, &m.pop_w_mid4, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, 64, 4) &&
+           encode4(fn, &m.ref_w_row, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K, c->N,
+                   64, 1) &&
+           encode4(fn, &m.ref_w_mid4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K, c->N,
+                   64, 4);
     if (!ok) return false;
   }
   return true;

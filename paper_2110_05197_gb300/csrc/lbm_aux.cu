@@ -391,13 +391,16 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
       }
       if (a.model == LBM_MODEL_SC_MR) {
         // self forces of Eqs. doublebeltattractiveforce / doublebeltrepulsionforce with
-        // Psi_s = rho_0 (1 - exp(-rho_s / rho_0)); a wall neighbour takes the centre value
+        // Psi_s = rho_0 (1 - exp(-rho_s / rho_0)), evaluated in the step's compute type C
+        // (FP64 only for FP64 storage: 92 exponentials per node); a wall neighbour takes
+        // the centre value
         for (int sp = 0; sp < 2; sp++) {
           const double* rs = sp ? rb : rr;
-          const double pc = a.rho0 * (1.0 - exp(-rs[n] / a.rho0));
+          const C r0 = C(a.rho0), ir0 = C(1.0 / a.rho0);
+          const double pc = double(r0 * (C(1) - exp(-C(rs[n]) * ir0)));
           auto psi_at = [&](int dx, int dy, int dz) {
             const long long m = nb_index(x, y, z, dx, dy, dz, a.nx, a.ny, a.nz);
-            return (solid && solid[m]) ? pc : a.rho0 * (1.0 - exp(-rs[m] / a.rho0));
+            return (solid && solid[m]) ? pc : double(r0 * (C(1) - exp(-C(rs[m]) * ir0)));
           };
           double att[3] = {0.0, 0.0, 0.0}, rep[3] = {0.0, 0.0, 0.0};
           for (int q = 0; q < L::NP; q++) {

@@ -112,9 +112,8 @@ cudaError_t launch_tma_t(lbm_ctx* c) {
 }
 
 // TMA-staged kernel with the x-halo exchanged inside a cluster of nx / 32 blocks.
-template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TY>
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
 cudaError_t launch_tmac_t(lbm_ctx* c) {
-  constexpr int TX = kTmaTX;
   constexpr size_t smem = tmac_smem_bytes<L, T, S, RT, MODEL, WALLS, TX, TY>();
   auto kern = step_kernel_tmac<L, T, S, RT, MODEL, WALLS, TX, TY>;
   static bool attr_set = false;
@@ -222,12 +221,14 @@ cudaError_t launch_step_t(lbm_ctx* c) {
   } else {
   if (c->aa) return launch_fp_t<L, T, S, RT, MODEL, WALLS, REP>(c);
   if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
-    if (c->tma_ok && c->tx == kTmaTX && c->ty == 4 && c->p.nx / kTmaTX <= kMaxCluster &&
-        (long long)c->K * c->Q * c->N < (1LL << 31))
-      return launch_tmac_t<L, T, S, RT, MODEL, WALLS, 4>(c);
+    const bool small_index = (long long)c->K * c->Q * c->N < (1LL << 31);
+    if (c->tma_ok && c->tx == 64 && c->ty == 4 && c->p.nx % 64 == 0 && c->p.nx / 64 <= kMaxCluster && small_index)
+      return launch_tmac_t<L, T, S, RT, MODEL, WALLS, 64, 4>(c);
+    if (c->tma_ok && c->tx == kTmaTX && c->ty == 4 && c->p.nx / kTmaTX <= kMaxCluster && small_index)
+      return launch_tmac_t<L, T, S, RT, MODEL, WALLS, kTmaTX, 4>(c);
     if (c->tma_ok && c->tx == kTmaTX && c->ty == kTmaTY) {
       if (c->p.nx / kTmaTX <= kMaxCluster && (long long)c->K * c->Q * c->N < (1LL << 31))
-        return launch_tmac_t<L, T, S, RT, MODEL, WALLS, kTmaTY>(c);
+        return launch_tmac_t<L, T, S, RT, MODEL, WALLS, kTmaTX, kTmaTY>(c);
       return launch_tma_t<L, T, S, RT, MODEL, WALLS>(c);
     }
   }

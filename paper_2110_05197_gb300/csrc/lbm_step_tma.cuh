@@ -27,8 +27,9 @@ namespace lbm {
 // Tensor maps for one population buffer and its reference field: main-column boxes of
 // a single row and of TY rows.
 struct TmaMaps {
-  CUtensorMap pop_main_row, pop_main_mid, pop_main_mid4;  // rows 1, 8, 4
+  CUtensorMap pop_main_row, pop_main_mid, pop_main_mid4;  // 32 columns, rows 1, 8, 4
   CUtensorMap ref_main_row, ref_main_mid, ref_main_mid4;
+  CUtensorMap pop_w_row, pop_w_mid4, ref_w_row, ref_w_mid4;  // 64 columns, rows 1, 4 (nx % 64 == 0)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

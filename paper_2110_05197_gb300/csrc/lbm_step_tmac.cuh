@@ -94,9 +94,9 @@ constexpr int kClusterFieldSlots = 5;
 // a few spilled registers.  With 32 x 4 tiles two blocks of half the size share an SM:
 // each cluster's lockstep stalls are then covered by the other cluster's work, which pays
 // where clusters are large (nx = 256: C = 8).
-template <int MODEL, class S, int TY>
+template <int MODEL, class S, int TX, int TY>
 __host__ __device__ constexpr int tmac_min_blocks() {
-  return TY <= 4 ? 2 : ((ModelTraits<MODEL>::K == 1 || sizeof(S) == 2) ? 2 : 1);  // 3 measured no faster
+  return TX * TY <= 128 ? 2 : ((ModelTraits<MODEL>::K == 1 || sizeof(S) == 2) ? 2 : 1);  // 3 measured no faster
 }
 
 // Raw plane buffers: as many as the block's share of shared memory holds, 2 to 6.  The
@@ -107,10 +107,22 @@ __host__ __device__ constexpr int tmac_raw_slots() {
   using Lay = TmaLayout<L, S, RT, MODEL, TX, TY>;
   constexpr int NV = ModelTraits<MODEL>::NF + ModelTraits<MODEL>::K;
   // per-block share of the SM's 228 KB (1 KB of it reserved per block), 227 KB at most
-  constexpr size_t budget = tmac_min_blocks<MODEL, S, TY>() == 1 ? 232448 : (233472 / tmac_min_blocks<MODEL, S, TY>() - 1024);
+  constexpr size_t budget = tmac_min_blocks<MODEL, S, TX, TY>() == 1 ? 232448 : (233472 / tmac_min_blocks<MODEL, S, TX, TY>() - 1024);
   constexpr size_t fixed = kClusterHeader + kClusterFieldSlots * NV * Lay::NE * sizeof(T) + (WALLS ? kClusterFieldSlots * Lay::NE : 0);
   constexpr size_t n = (budget - fixed) / Lay::BUF_MAIN;
   return n > 6 ? 6 : int(n);
+}
+
+// Tensor maps of the tile shape: main columns of one row (halo rows) or of the TY rows.
+template <int TX, int TY>
+__device__ __forceinline__ const CUtensorMap* tmac_pop_map(const TmaMaps& m, bool mid) {
+  if constexpr (TX == 64) return mid ? &m.pop_w_mid4 : &m.pop_w_row;
+  return mid ? (TY == 4 ? &m.pop_main_mid4 : &m.pop_main_mid) : &m.pop_main_row;
+}
+template <int TX, int TY>
+__device__ __forceinline__ const CUtensorMap* tmac_ref_map(const TmaMaps& m, bool mid) {
+  if constexpr (TX == 64) return mid ? &m.ref_w_mid4 : &m.ref_w_row;
+  return mid ? (TY == 4 ? &m.ref_main_mid4 : &m.ref_main_mid) : &m.ref_main_row;
 }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
@@ -127,13 +139,13 @@ __host__ __device__ constexpr size_t tmac_smem_bytes() {
 // tile-row-planes [c*U/nblk, (c+1)*U/nblk), U = ncol * nz.
 // Staging warps: 8 for two population sets (the staging of plane J+1 gates the collision
 // of plane J), 4 where two blocks share an SM.
-template <int MODEL, class S, int TY>
-__host__ __device__ constexpr int tmac_stage_warps() { return tmac_min_blocks<MODEL, S, TY>() == 1 ? 8 : 4; }
 template <int MODEL, class S, int TX, int TY>
-__host__ __device__ constexpr int tmac_threads() { return TX * TY + 32 * (tmac_stage_warps<MODEL, S, TY>() + 1); }
+__host__ __device__ constexpr int tmac_stage_warps() { return tmac_min_blocks<MODEL, S, TX, TY>() == 1 ? 8 : 4; }
+template <int MODEL, class S, int TX, int TY>
+__host__ __device__ constexpr int tmac_threads() { return TX * TY + 32 * (tmac_stage_warps<MODEL, S, TX, TY>() + 1); }
 
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, int TX, int TY>
-__global__ void __launch_bounds__(tmac_threads<MODEL, S, TX, TY>(), tmac_min_blocks<MODEL, S, TY>())
+__global__ void __launch_bounds__(tmac_threads<MODEL, S, TX, TY>(), tmac_min_blocks<MODEL, S, TX, TY>())
     step_kernel_tmac(const __grid_constant__ TmaMaps maps, S* __restrict__ fout, RT* __restrict__ rout,
                      const uint8_t* __restrict__ solid, int* __restrict__ status, StepParams<T> p) {
   constexpr int kCollideWarps = TX * TY / 32;  // one collision thread per tile node
@@ -145,7 +157,7 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S, TX, TY>(), tmac_min_blo
   constexpr int NF = ModelTraits<MODEL>::NF, NV = NF + K;
   constexpr int EX = Lay::EX, NE = Lay::NE;
   constexpr int kRawSlots = tmac_raw_slots<L, T, S, RT, MODEL, WALLS, TX, TY>();
-  constexpr int kStageWarps = tmac_stage_warps<MODEL, S, TY>();
+  constexpr int kStageWarps = tmac_stage_warps<MODEL, S, TX, TY>();
   static_assert(kRawSlots >= 2, "at least two raw plane buffers");
   static_assert(2 * kRawSlots + 3 * kClusterFieldSlots <= kClusterHeader / 8, "mbarriers fit the header");
   // A blown-up (or timed-out) state stops stepping.  Blocks of one cluster may read the
@@ -221,8 +233,8 @@ __global__ void __launch_bounds__(tmac_threads<MODEL, S, TX, TY>(), tmac_min_blo
           for (int g = 0; g < 3; g++) {
             const bool mid = g == 1;
             const int y = g == 0 ? yt : (g == 1 ? y0 : yb);
-            tma_load_4d(b + Lay::PM::group(g), mid ? (TY == 4 ? &maps.pop_main_mid4 : &maps.pop_main_mid) : &maps.pop_main_row, x0, 0, y, gz, bar);
-            tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), mid ? (TY == 4 ? &maps.ref_main_mid4 : &maps.ref_main_mid) : &maps.ref_main_row, x0, 0,
+            tma_load_4d(b + Lay::PM::group(g), tmac_pop_map<TX, TY>(maps, mid), x0, 0, y, gz, bar);
+            tma_load_4d(b + Lay::OFF_RM + Lay::RMR::group(g), tmac_ref_map<TX, TY>(maps, mid), x0, 0,
                         y, gz, bar);
           }
         }

@@ -154,18 +154,20 @@ def test_tiling_does_not_change_results(lbm, precision, shape):
     fetched halo columns at nx = 288) for two z-chunk lengths, each also as a persistent
     grid (tz = 0; at 96 x 64 x 48 every block's share spans several columns).  Up to
     nx = 256 the cluster kernel also runs 32 x 4 tiles (two blocks per SM), which must give
-    the same bits as its 32 x 8 tiles.  The staged and generic kernels inline the same
+    the same bits as its 32 x 8 tiles, and, where nx % 64 == 0, 64 x 4 tiles in clusters of
+    nx / 64 blocks.  The staged and generic kernels inline the same
     per-node code but the compiler fuses multiply-adds differently, so across kernels the
     states agree to a few ulps of the stored deviations."""
     case = C.cg_drop3d(*shape)
     tma = shape[0] % 32 == 0 and shape[1] % 8 == 0 and precision != 0
     cluster = tma and shape[0] <= 256
-    generic = [(64, 4, 5), (32, 2, 19), (128, 2, 1), (64, 4, 0)]
+    wide = cluster and shape[0] % 64 == 0       # 64 x 4 tiles in clusters of nx / 64
+    generic = [(32, 2, 19), (128, 2, 1)]
     staged = [(32, 8, 16), (32, 8, 3), (32, 8, 0)]
-    if cluster:
-        staged += [(32, 4, 0), (32, 4, 7)]
-    else:
-        generic += [(32, 4, 0)]
+    staged += [(32, 4, 0), (32, 4, 7)] if cluster else []
+    generic += [] if cluster else [(32, 4, 0)]
+    staged += [(64, 4, 5), (64, 4, 0)] if wide else []
+    generic += [] if wide else [(64, 4, 5), (64, 4, 0)]
     outs = {}
     for tiling in generic + staged:
         lat = C.gpu_lattice(lbm, case, precision)
@@ -183,18 +185,22 @@ def test_tiling_does_not_change_results(lbm, precision, shape):
         assert d <= {1: 1e-6, 2: 2e-4}[precision] * scale
 
 
-@pytest.mark.parametrize("name", ["cg_tma3d", "cg_tma_walls", "sc_tma3d", "sc2c_tma3d"])
-def test_cluster_kernel_32x4_tiles(orc, lbm, name):
-    """The cluster kernel with 32 x 4 tiles (two blocks per SM; the autotuner's pick where
-    clusters are large) against the oracle after 100 FP32 steps, and bit for bit against
-    its 32 x 8 tiles in FP32 and FP16."""
-    case = C.SMALL_CASES[name]()
+@pytest.mark.parametrize("tiling", [(32, 4, 0), (64, 4, 0)])
+@pytest.mark.parametrize("name", ["cg_tma3d", "cg_tma_walls", "sc_tma3d", "sc2c_tma3d", "cg_tma64"])
+def test_cluster_kernel_other_tiles(orc, lbm, name, tiling):
+    """The cluster kernel with 32 x 4 tiles (two blocks per SM) and with 64 x 4 tiles
+    (clusters of nx / 64 blocks; the autotuner's picks for large clusters and for the
+    128^3 benchmark lattice) against the oracle after 100 FP32 steps, and bit for bit
+    against its 32 x 8 tiles in FP32 and FP16."""
+    case = C.cg_drop3d(nx=64, ny=16, nz=9) if name == "cg_tma64" else C.SMALL_CASES[name]()
+    if tiling[0] == 64 and case.kw["nx"] % 64:
+        pytest.skip("64-column tiles need nx % 64 == 0")
     s = C.oracle_sim(orc, case).step(100)
     for precision in (lbm.FP32, lbm.FP16):
         a = C.gpu_lattice(lbm, case, precision)
         b = C.gpu_lattice(lbm, case, precision)
         a.set_tiling(32, 8, 0)
-        b.set_tiling(32, 4, 0)
+        b.set_tiling(*tiling)
         a.step(100)
         b.step(100)
         assert np.array_equal(a.pops().cpu().numpy(), b.pops().cpu().numpy())
@@ -207,7 +213,7 @@ def test_cluster_kernel_32x4_tiles(orc, lbm, name):
             er = np.max((np.abs(rr - orr) / np.maximum(np.abs(orr), 1e-3 * scale))[fl])
             eb = np.max((np.abs(rb - orb) / np.maximum(np.abs(orb), 1e-3 * scale))[fl])
             eu2 = np.linalg.norm(u - ou) / np.linalg.norm(ou)
-            print(f"{name} 32x4 FP32: rho err {er:.2e}/{eb:.2e}, u err L2 {eu2:.2e}")
+            print(f"{name} {tiling[0]}x{tiling[1]} FP32: rho err {er:.2e}/{eb:.2e}, u err L2 {eu2:.2e}")
             assert er < 1e-5 and eb < 1e-5 and eu2 < 1e-5
 
 
