@@ -300,6 +300,16 @@ def multirange_steps(dev, stream, steps: int = 20):
     return out
 
 
+def workload_config(ws: int) -> dict:
+    """The benchmark workload, the same for both arms (the reference arm times a slab of it,
+    stated in its cpu_baseline sample)."""
+    return {"workload": "D3Q19 CG + SC multiphase oscillating droplet, 128^3 each, FP32",
+            "lattice": "D3Q19", "nx": N3, "ny": N3, "nz": N3, "density_ratio": 10,
+            "cg": {"A": 5e-3, "tau": 1.0, "beta": 0.7}, "sc": {"G": -5.0, "rho0": 1.0, "tau": 1.0},
+            "l2": "inputs larger than L2 (477 MB of populations per step)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -311,8 +321,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "D3Q19 CG+SC oscillating droplet (oracle sample)",
-                                            "nodes_per_lattice": n},
+            "data": "synthetic", "config": workload_config(1),
             "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -453,11 +462,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "D3Q19 CG + SC multiphase oscillating droplet, 128^3 each, FP32",
-                       "lattice": "D3Q19", "nx": N3, "ny": N3, "nz": N3, "density_ratio": 10,
-                       "cg": {"A": 5e-3, "tau": 1.0, "beta": 0.7}, "sc": {"G": -5.0, "rho0": 1.0, "tau": 1.0},
-                       "l2": "inputs larger than L2 (477 MB of populations per step)",
-                       "parallelism": f"replicas x{ws}"},
+            "config": workload_config(ws),
             "cg_mlups": n / (cg_avg / 1e3) / 1e6, "sc_mlups": n / (sc_avg / 1e3) / 1e6,
             "cg_step_ms": cg_avg, "sc_step_ms": sc_avg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
