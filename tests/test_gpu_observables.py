@@ -3,7 +3,7 @@ Laplace pressure jump of the static droplet (Sec. 3.1), the oscillation frequenc
 deformed droplet (Sec. 3.2) and the satellite-droplet mass of a broken jet (Sec. 3.4).
 Each test runs the oracle once and the GPU path in FP64, FP32, FP16 and BF16 storage on
 the same seeded input, prints the relative error of the observable and holds it to the
-bound stated in ERR_BOUND (measured errors are listed in DESIGN's precision section).
+bound stated in ERR_BOUND (about three times the measured error).
 
 Workloads: the D2Q9 128^2 droplet of radius 20 for its full 2000 steps; a 48^3 D3Q19
 ellipsoid (semi-axes 13.2/11.4/11.4, ratio 10, tau 0.6) over 2400 steps, radius along x
