@@ -107,3 +107,20 @@ def test_sweep_trace_is_seeded_and_in_range():
         else:
             assert 4.2 <= -r.kw["G"] <= 6.5
     assert {r.model for r in a} == {lbm.CG, lbm.SC_MP}
+
+
+def test_tuner_candidates():
+    from paper_2110_05197_gb300 import tune
+    c = tune.candidates_for(lbm.Params(nx=128, ny=128, nz=128))
+    assert (32, 8, 0) in c and (64, 4, 0) in c and (32, 4, 0) in c
+    # the field-pass kernels (in-place streaming, multirange model) pick their own shape
+    assert tune.candidates_for(lbm.Params(nx=64, ny=64, nz=64, streaming=lbm.STREAM_AA)) == [(32, 8, 0)]
+    assert tune.candidates_for(lbm.Params(nx=64, ny=64, nz=64, model=lbm.SC_MR)) == [(32, 8, 0)]
+
+
+def test_multirange_workspace_and_limits(L):
+    rc, b = _size(L, nx=64, ny=64, nz=64, model=lbm.SC_MR, precision=lbm.FP32)
+    rc2, b2 = _size(L, nx=64, ny=64, nz=64, model=lbm.SC_2C, precision=lbm.FP32)
+    assert rc == rc2 == lbm.OK and b == b2      # same storage as the two-component model
+    rc, _ = _size(L, nx=1, ny=64, nz=64, model=lbm.SC_MR)
+    assert rc == lbm.EINVAL                     # the repulsion reaches two nodes
