@@ -243,13 +243,24 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, const uint8_t* solid);
  *   solid  : DEVICE pointer to the uint8 wall mask [N], or NULL.
  *   totals : host or device pointer to LBM_NTOTALS doubles (written).
  *   stream : cudaStream_t the work is enqueued on; the call synchronises it.
- * Scratch lives in one static __device__ array of 16 MiB + 96 KiB per device that loads
- * the library, held until process exit; nothing is allocated by the call.  The first call
+ * Scratch lives in one static __device__ array per device that loads the library, held
+ * until process exit: 2 * LBM_NOALLOC_MAX_NODES FP64 densities (16 MiB), 1184 blocks x
+ * LBM_NTOTALS FP64 partial sums (94,720 bytes) and a 256-byte result record, 16,872,192
+ * bytes in all; nothing is allocated by the call.  The first call
  * on a device looks up that array's address (cudaGetSymbolAddress, with the caller's
  * device current) and so should come before any stream capture on that device.  Calls
  * share the array: calls that overlap on the GPU race and must be serialised.
- * Errors: LBM_EINVAL for NULL/host pops, N > LBM_NOALLOC_MAX_NODES or bad sizes;
- * LBM_ECUDA on a CUDA error; LBM_EUNSTABLE when the blow-up check trips (totals written). */
+ * The totals agree with lbm_moments' to rounding of the FP64 sums (about 1e-12 relative
+ * on masses, E_kin, max|u| and minimum densities; momentum to 1e-13 of the mass): both sum
+ * momentum as opposite-pair differences, but from different inputs (canonical FP64
+ * populations here, the stored deviations there).
+ * Not supported: the multirange SC model (LBM_MODEL_SC_MR) and CG with the repulsion force
+ * (rep_pi != 0), whose force enters u and E_kin; both give LBM_EINVAL.
+ * Errors: LBM_EINVAL for NULL pops or totals, pops or solid not in the memory of the current
+ * device (host memory, or device memory of another GPU; managed memory is accepted),
+ * N > LBM_NOALLOC_MAX_NODES, bad sizes or an unsupported model; LBM_ECUDA on a CUDA error;
+ * LBM_EUNSTABLE when the blow-up check trips (totals written).  The call cannot know the
+ * sizes of pops and solid: they must hold K*Q*N doubles and N bytes. */
 enum { LBM_NOALLOC_MAX_NODES = 1 << 20 };
 lbm_status lbm_totals_noalloc(const lbm_params* p, const double* pops, const uint8_t* solid, double* totals,
                               void* stream);

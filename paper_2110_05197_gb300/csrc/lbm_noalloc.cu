@@ -92,16 +92,22 @@ __global__ void __launch_bounds__(kThreads) part_kernel(const double* __restrict
   double acc[LBM_NTOTALS] = {0, 0, 0, 0, 0, 0, 0, 0, INFINITY, INFINITY};
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
     if (solid && solid[n]) continue;
+    // momentum as opposite-pair differences f_i - f_opp(i), as lbm_moments sums it: the
+    // symmetric (rest-state) part of each pair cancels exactly before it is accumulated
     double j[3] = {0.0, 0.0, 0.0};
     int bad = 0;
-    for (int k = 0; k < a.K; k++)
-      for (int i = 0; i < L::Q; i++) {
-        const double v = f[(long long)(k * L::Q + i) * a.n + n];
-        if (!isfinite(v)) bad = 1;
-        j[0] += cx<L>(i) * v;
-        j[1] += cy<L>(i) * v;
-        j[2] += cz<L>(i) * v;
+    for (int k = 0; k < a.K; k++) {
+      if (!isfinite(f[(long long)(k * L::Q) * a.n + n])) bad = 1;
+      for (int q = 0; q < L::NP; q++) {
+        const double vp = f[(long long)(k * L::Q + 2 * q + 1) * a.n + n];
+        const double vm = f[(long long)(k * L::Q + 2 * q + 2) * a.n + n];
+        if (!isfinite(vp) || !isfinite(vm)) bad = 1;
+        const double d = vp - vm;
+        j[0] += L::pcx(q) * d;
+        j[1] += L::pcy(q) * d;
+        j[2] += L::pcz(q) * d;
       }
+    }
     const double r = rr[n], b = rb[n], rho = r + b;
     double F[3] = {a.body[0], a.body[1], a.body[2]};
     if (a.model != LBM_MODEL_CG) {
@@ -183,13 +189,17 @@ cudaError_t scratch_on_current_device(unsigned char** out) {
   return cudaSuccess;
 }
 
-bool is_device(const void* ptr) {
+// True for managed memory and for device memory of device `dev` (the current device, on
+// which the kernels run); a device pointer of another GPU would be read without peer
+// access, so it is refused like a host pointer.
+bool is_device(const void* ptr, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -203,7 +213,13 @@ extern "C" lbm_status lbm_totals_noalloc(const lbm_params* p, const double* pops
   const long long n = (long long)p->nx * p->ny * p->nz;
   if (n > kMaxNodes) return LBM_EINVAL;  // beyond the fixed scratch (LBM_NOALLOC_MAX_NODES)
   if (p->model != LBM_MODEL_CG && !(p->rho0_psi > 0)) return LBM_EINVAL;
-  if (!is_device(pops) || (solid && !is_device(solid))) return LBM_EINVAL;
+  // the CG repulsion force (Sec. 2.3) enters u and E_kin; this entry point does not
+  // compute it, so such a state is refused rather than given different totals
+  if (p->model == LBM_MODEL_CG && p->rep_pi != 0.0) return LBM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+  if (!is_device(pops, dev) || (solid && !is_device(solid, dev))) return LBM_EINVAL;
+  const bool dev_totals = is_device(totals, dev);
 
   unsigned char* base = nullptr;
   cudaError_t e = scratch_on_current_device(&base);
@@ -241,7 +257,7 @@ extern "C" lbm_status lbm_totals_noalloc(const lbm_params* p, const double* pops
   e = cudaGetLastError();
   if (e != cudaSuccess) return LBM_ECUDA;
   Record host;
-  if (is_device(totals)) {
+  if (dev_totals) {
     e = cudaMemcpyAsync(totals, rec->totals, sizeof(host.totals), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&host.status, &rec->status, sizeof(int), cudaMemcpyDeviceToHost, s);
   } else {
@@ -249,7 +265,7 @@ extern "C" lbm_status lbm_totals_noalloc(const lbm_params* p, const double* pops
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return LBM_ECUDA;
-  if (!is_device(totals))
+  if (!dev_totals)
     for (int k = 0; k < LBM_NTOTALS; k++) totals[k] = host.totals[k];
   return host.status ? LBM_EUNSTABLE : LBM_OK;
 }

@@ -81,12 +81,47 @@ SIGNATURES = {
 NOALLOC_MAX_NODES = 1 << 20
 
 
+def _noalloc_args(params: "Params", pops, solid, out, stream):
+    """Check what lbm_totals_noalloc cannot check itself (it gets raw pointers): dtypes,
+    contiguity, sizes and that every device tensor is on the current device."""
+    import torch
+
+    def bad(why):
+        raise LbmError(EINVAL, f"lbm_totals_noalloc: {why}")
+
+    if not isinstance(pops, torch.Tensor) or not pops.is_cuda:
+        bad("pops must be a CUDA tensor")
+    dev = torch.cuda.current_device()
+    if pops.device.index != dev:
+        bad(f"pops is on cuda:{pops.device.index}, the current device is cuda:{dev}")
+    if pops.dtype != torch.float64 or not pops.is_contiguous():
+        bad("pops must be a contiguous float64 tensor")
+    if pops.numel() < params.ncomp * params.q * params.n:
+        bad(f"pops holds {pops.numel()} values, K*Q*N = {params.ncomp * params.q * params.n}")
+    if solid is not None:
+        if not isinstance(solid, torch.Tensor) or not solid.is_cuda or solid.device.index != dev:
+            bad("solid must be a CUDA tensor on the current device")
+        if solid.dtype != torch.uint8 or not solid.is_contiguous() or solid.numel() < params.n:
+            bad("solid must be a contiguous uint8 tensor of N values")
+    if isinstance(out, torch.Tensor):
+        if not out.is_cuda or out.device.index != dev or out.dtype != torch.float64 or \
+                not out.is_contiguous() or out.numel() < NTOTALS:
+            bad("a device out must be a contiguous float64 CUDA tensor of NTOTALS values on the current device")
+    elif not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous and
+              out.size >= NTOTALS):
+        bad("a host out must be a contiguous float64 array of NTOTALS values")
+    if stream is not None and stream.device.index != dev:
+        bad("the stream belongs to another device")
+
+
 def totals_noalloc(params: "Params", pops, solid=None, out=None, stream=None):
     """lbm_totals_noalloc: totals of caller-owned canonical FP64 populations on the device,
-    using the library's static scratch (no allocation).  Returns (totals, status)."""
+    using the library's static scratch (no allocation).  Returns (totals, status).
+    Raises LbmError(EINVAL) for a wrong dtype, size, layout or device before the call."""
     cp = params.to_c()
     if out is None:
         out = np.zeros(NTOTALS)
+    _noalloc_args(params, pops, solid, out, stream)
     s = stream.cuda_stream if stream is not None else None
     rc = lib().lbm_totals_noalloc(ctypes.byref(cp), _ptr(pops), _ptr(solid), _ptr(out), s)
     if rc not in (OK, EUNSTABLE):

@@ -5,6 +5,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2110_05197_gb300 import build as lbm_build
@@ -124,3 +125,14 @@ def test_multirange_workspace_and_limits(L):
     assert rc == rc2 == lbm.OK and b == b2      # same storage as the two-component model
     rc, _ = _size(L, nx=1, ny=64, nz=64, model=lbm.SC_MR)
     assert rc == lbm.EINVAL                     # the repulsion reaches two nodes
+
+
+def test_noalloc_binding_refuses_host_buffers(L):
+    """The binding checks what the C entry point cannot (it receives raw pointers): a host
+    tensor or array is refused before any call, on any machine."""
+    torch = pytest.importorskip("torch")
+    p = lbm.Params(nx=4, ny=4, nz=4)
+    for pops in (torch.zeros(2 * 19 * p.n, dtype=torch.float64), np.zeros(2 * 19 * p.n)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.totals_noalloc(p, pops)
+        assert e.value.status == lbm.EINVAL
