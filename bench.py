@@ -424,10 +424,15 @@ def run_ours(args):
     value = job_mlups(n, 2, K, ws, total_ms / 1e3)
     peak, peak_kind = hbm_peak()
     # 32 x 8, 32 x 4 and 64 x 4 tiles run the cluster TMA kernel on this 128^3 lattice
-    # (clusters of nx / tx <= 8 blocks); the label names the tile, whose traffic differs
+    # (clusters of nx / tx <= 8 blocks), 32 x 16 tiles the ring kernel; the label names
+    # the tile, whose traffic differs
     tx_ty = list(tiling["cg"][:2])
-    cg_kernel = (f"step_kernel_tmac<D3Q19,float,CG,{tx_ty[0]}x{tx_ty[1]}>"
-                 if tx_ty in ([32, 8], [32, 4], [64, 4]) else "step_kernel<D3Q19,float,CG>")
+    if tx_ty in ([32, 8], [32, 4], [64, 4]):
+        cg_kernel = f"step_kernel_tmac<D3Q19,float,CG,{tx_ty[0]}x{tx_ty[1]}>"
+    elif tx_ty == [32, 16]:
+        cg_kernel = "step_kernel_ring<D3Q19,float,CG,32x16>"
+    else:
+        cg_kernel = "step_kernel<D3Q19,float,CG>"
     achieved = BYTES_PER_LU["cg"] * n / (cg_avg / 1e3) / 1e9
     tot_cg, rc_cg = cg.totals()
     tot_sc, rc_sc = sc.totals()

@@ -203,6 +203,16 @@ bool build_tma_maps(lbm_ctx* c) {
            encode4(fn, &m.ref_w_mid4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K, c->N,
                    64, 4);
     if (!ok) return false;
+    // tiles of the ring kernel (lbm_step_ring.cuh); optional: without them that kernel is
+    // not used
+    m.mid16 = p.ny % 16 == 0 &&
+              encode4(fn, &m.pop_main_mid16, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, kTmaTX, 16) &&
+              encode4(fn, &m.ref_main_mid16, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
+                      c->N, kTmaTX, 16);
+    m.w_mid8 = p.nx % 64 == 0 && p.ny % 8 == 0 &&
+               encode4(fn, &m.pop_w_mid8, dt, c->elt, c->f[b], p.nx, p.ny, p.nz, K * Q, c->N, 64, 8) &&
+               encode4(fn, &m.ref_w_mid8, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->relt, c->r[b], p.nx, p.ny, p.nz, K,
+                       c->N, 64, 8);
   }
   return true;
 }
@@ -262,7 +272,11 @@ lbm_status lbm_create(const lbm_params* p, void* ws, size_t* ws_bytes, void* str
 
 lbm_status lbm_set_tiling(lbm_ctx* c, int32_t tx, int32_t ty, int32_t tz) {
   if (!c) return LBM_EINVAL;
-  if (tx < 1 || ty < 1 || tz < 0 || tx * ty > 256 || (tx * ty) % 32 != 0) return LBM_EINVAL;
+  // 512-node tiles (32 x 16, 64 x 8) select the ring kernel; where it does not apply the
+  // step runs the 32 x 8 tiling instead
+  const bool ring = (tx == 32 && ty == 16) || (tx == 64 && ty == 8);
+  if (tx < 1 || ty < 1 || tz < 0 || (tx * ty > 256 && !ring) || (tx * ty) % 32 != 0) return LBM_EINVAL;
+  if (ring && c->p.lattice != LBM_D3Q19) return LBM_EINVAL;
   if (c->p.lattice == LBM_D2Q9 && tz > 1) return LBM_EINVAL;
   c->tx = tx;
   c->ty = ty;

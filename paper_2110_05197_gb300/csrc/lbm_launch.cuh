@@ -6,6 +6,7 @@
 
 #include "lbm_internal.cuh"
 #include "lbm_step_aa.cuh"
+#include "lbm_step_ring.cuh"
 #include "lbm_step_tmac.cuh"
 
 namespace lbm {
@@ -159,6 +160,71 @@ cudaError_t launch_tmac_t(lbm_ctx* c) {
   return cudaLaunchKernelEx(&cfg, kern, c->tma[c->cur], fout, rout, c->solid, &c->diag->status, sp);
 }
 
+// Ring kernel (lbm_step_ring.cuh): 512-node tiles (one block per SM) or 256-node tiles
+// (two), 2 to 4 raw plane buffers, clusters of nx / TX blocks.
+template <class L, class T, class S, class RT, int MODEL, int TX, int TY>
+cudaError_t launch_ring_t(lbm_ctx* c) {
+  constexpr size_t smem = ring_smem_bytes<L, S, RT, MODEL, TX, TY>();
+  auto kern = step_kernel_ring<L, T, S, RT, MODEL, TX, TY>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int C = c->p.nx / TX;
+  StepParams<T> sp = make_step_params<T>(c);
+  sp.ncx = C;               // blocks per cluster
+  sp.ncol = c->p.ny / TY;   // tile rows: the work partition's columns
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(TX * TY, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (c->tz > 0) {
+    sp.nblk = sp.ncol * sp.nchunks;  // one unit (tile row, tz planes) per cluster
+  } else {
+    const void* fn = reinterpret_cast<const void*>(kern);
+    if (c->occ_fn != fn || c->occ_tx != -C) {
+      int ncl = 0;
+      cfg.gridDim = dim3(C, 1, 1);
+      cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      c->occ_fn = fn;
+      c->occ_tx = -C;
+      c->occ_ty = 0;
+      c->occ_blocks = ncl > 0 ? ncl : 1;
+    }
+    persistent_plan(sp, c->occ_blocks);  // clusters
+  }
+  cfg.gridDim = dim3(sp.nblk * C, 1, 1);
+  S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
+  RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
+  return cudaLaunchKernelEx(&cfg, kern, c->tma[c->cur], fout, rout, &c->diag->status, sp);
+}
+
+// Whether the ring kernel runs this context with TX x TY tiles.
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, int TX, int TY>
+bool ring_eligible(const lbm_ctx* c) {
+  if constexpr (L::D != 3 || sizeof(T) != 4 || WALLS || REP || !(MODEL == kCG || MODEL == kSCMP)) {
+    return false;
+  } else {
+    if (ring_raw<L, S, RT, MODEL, TX, TY>() < 2) return false;  // two plane buffers do not fit
+    // 64 x 4 and 32 x 8 tiles use the maps every TMA-eligible lattice has (64-column
+    // maps where nx % 64 == 0)
+    const bool maps = TX == 64 ? (TY == 8 ? c->tma[0].w_mid8 && c->tma[1].w_mid8 : c->p.nx % 64 == 0)
+                               : (TY == 16 ? c->tma[0].mid16 && c->tma[1].mid16 : true);
+    return c->tma_ok && maps && !c->aa && c->p.nx % TX == 0 && c->p.ny % TY == 0 &&
+           c->p.nx / TX <= kMaxCluster && (long long)c->K * c->Q * c->N < (1LL << 31);
+  }
+}
+
 // Field-pass step (in-place streaming, or the multirange model): the field pass, then the
 // step kernel, both over all nodes.
 template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
@@ -220,6 +286,34 @@ cudaError_t launch_step_t(lbm_ctx* c) {
     return launch_fp_t<L, T, S, RT, MODEL, WALLS, REP>(c);
   } else {
   if (c->aa) return launch_fp_t<L, T, S, RT, MODEL, WALLS, REP>(c);
+  if (c->tx * c->ty > 256) {
+    // a ring tiling: the ring kernel where it applies, else the 32 x 8 persistent tiling
+    if constexpr (L::D == 3 && sizeof(T) == 4 && !WALLS && !REP && (MODEL == kCG || MODEL == kSCMP)) {
+      if constexpr (ring_raw<L, S, RT, MODEL, 32, 16>() >= 2)
+        if (c->tx == 32 && ring_eligible<L, T, S, RT, MODEL, WALLS, REP, 32, 16>(c))
+          return launch_ring_t<L, T, S, RT, MODEL, 32, 16>(c);
+      if constexpr (ring_raw<L, S, RT, MODEL, 64, 8>() >= 2)
+        if (c->tx == 64 && ring_eligible<L, T, S, RT, MODEL, WALLS, REP, 64, 8>(c))
+          return launch_ring_t<L, T, S, RT, MODEL, 64, 8>(c);
+    }
+    const int tx = c->tx, ty = c->ty, tz = c->tz;
+    c->tx = kTmaTX;
+    c->ty = kTmaTY;
+    c->tz = 0;
+    const cudaError_t e = launch_step_t<L, T, S, RT, MODEL, WALLS, REP>(c);
+    c->tx = tx;
+    c->ty = ty;
+    c->tz = tz;
+    return e;
+  }
+  if constexpr (L::D == 3 && sizeof(T) == 4 && !WALLS && !REP && (MODEL == kCG || MODEL == kSCMP)) {
+    // 64 x 4 tiles: the ring kernel (two blocks per SM) where two of its blocks fit an SM
+    // (every storage type for SC multiphase, 16-bit storage for CG); it gives the same bits
+    // as the cluster kernel, which keeps the other cases
+    if constexpr (ring_raw<L, S, RT, MODEL, 64, 4>() >= 2)
+      if (c->tx == 64 && c->ty == 4 && ring_eligible<L, T, S, RT, MODEL, WALLS, REP, 64, 4>(c))
+        return launch_ring_t<L, T, S, RT, MODEL, 64, 4>(c);
+  }
   if constexpr (L::D == 3 && sizeof(T) == 4 && !REP) {
     const bool small_index = (long long)c->K * c->Q * c->N < (1LL << 31);
     if (c->tma_ok && c->tx == 64 && c->ty == 4 && c->p.nx % 64 == 0 && c->p.nx / 64 <= kMaxCluster && small_index)

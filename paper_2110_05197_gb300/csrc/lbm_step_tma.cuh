@@ -30,6 +30,9 @@ struct TmaMaps {
   CUtensorMap pop_main_row, pop_main_mid, pop_main_mid4;  // 32 columns, rows 1, 8, 4
   CUtensorMap ref_main_row, ref_main_mid, ref_main_mid4;
   CUtensorMap pop_w_row, pop_w_mid4, ref_w_row, ref_w_mid4;  // 64 columns, rows 1, 4 (nx % 64 == 0)
+  CUtensorMap pop_main_mid16, ref_main_mid16;                  // 32 columns, 16 rows (ny % 16 == 0)
+  CUtensorMap pop_w_mid8, ref_w_mid8;                          // 64 columns, 8 rows (nx % 64 == 0)
+  bool mid16, w_mid8;                                          // which of the last two pairs are encoded
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

@@ -16,7 +16,8 @@ from . import lbm
 
 # tz = 0 selects the persistent grid (equal shares of all tile-planes per resident block)
 CANDIDATES_3D = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (16, 8, 0), (128, 2, 0),
-                 (32, 8, 16), (32, 8, 22), (32, 8, 32), (32, 4, 16), (64, 4, 16)]
+                 (32, 8, 16), (32, 8, 22), (32, 8, 32), (32, 4, 16), (64, 4, 16),
+                 (32, 16, 0), (64, 8, 0)]  # the last two: the ring kernel where it applies
 CANDIDATES_2D = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (128, 2, 0), (32, 8, 1), (32, 4, 1), (64, 4, 1), (128, 2, 1)]
 
 _cache: dict = {}

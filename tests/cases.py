@@ -167,3 +167,30 @@ def gpu_lattice(lbm, case: Case, precision: int, **extra):
 
     lat.init(t(case.rho_r), t(case.rho_b), t(case.u), t(case.solid, torch.uint8))
     return lat
+
+
+# Lattices for the ring kernel (512-node tiles, 32 x 16 or 64 x 8, clusters of nx / TX).
+RING_CASES = {
+    "cg_ring32": lambda: cg_drop3d(nx=32, ny=16, nz=13),                   # 32 x 16: cluster of 1
+    "cg_ring64": lambda: cg_drop3d(nx=64, ny=32, nz=10),                   # 32 x 16: 2; 64 x 8: 1
+    "cg_ring96": lambda: cg_drop3d(nx=96, ny=16, nz=7, ratio=3.0),         # 32 x 16: 3
+    "cg_ring_body": lambda: cg_drop3d(nx=32, ny=16, nz=9, body_force=(1e-5, 0.0, 2e-6)),
+    "sc_ring64": lambda: sc_mp3d(nx=64, ny=16, nz=14),                     # 32 x 16: 2; 64 x 8: 1
+}
+
+
+def ring_runs(kw: dict, precision: int, tiling) -> bool:
+    """Whether the library runs a tiling on the ring kernel: 32 x 16 and 64 x 8 tiles
+    (one block per SM; else it runs 32 x 8 tiles) and 64 x 4 tiles (two blocks per SM;
+    else the cluster kernel), for D3Q19, FP32/FP16/BF16 storage, CG or SC multiphase, no
+    walls, no repulsion force, two-buffer streaming, nx % TX == ny % TY == 0,
+    nx / TX <= 8, and a shared-memory footprint within the block's share: FP32 CG runs
+    only 32 x 16 tiles."""
+    tx, ty = tiling[0], tiling[1]
+    if kw.get("lattice", 1) != 1 or precision == 0 or kw.get("model", 0) not in (0, 1):
+        return False
+    if kw.get("rep_pi", 0.0) or kw.get("streaming", 0):
+        return False
+    if kw["nx"] % tx or kw["ny"] % ty or kw["nx"] // tx > 8:
+        return False
+    return not (kw.get("model", 0) == 0 and precision == 1 and tx == 64)
