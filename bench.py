@@ -249,6 +249,51 @@ def serving_sweep(n_req: int, seed: int = 5):
     return out
 
 
+def kernel_label(model: str, precision: int, tiling) -> str:
+    """The step kernel a tiling runs on the 128^3 benchmark lattices (nx / tx <= 8): the
+    ring kernel for 32 x 16 and 64 x 8 tiles, and for 64 x 4 tiles where two of its blocks
+    fit an SM (SC multiphase, or 16-bit storage); the cluster TMA kernel for the other
+    32 x 8, 32 x 4 and 64 x 4 tiles; the generic kernel otherwise.  The label names the
+    tile, whose traffic differs."""
+    tx, ty = int(tiling[0]), int(tiling[1])
+    elt = {1: "float", 2: "half", 3: "bf16"}[precision]
+    m = "CG" if model == "cg" else "SC-MP"
+    ring = (tx, ty) in ((32, 16), (64, 8)) or ((tx, ty) == (64, 4) and (model == "sc" or precision != 1))
+    if ring and not (model == "cg" and precision == 1 and tx == 64):
+        return f"step_kernel_ring<D3Q19,{elt},{m},{tx}x{ty}>"
+    if (tx, ty) in ((32, 8), (32, 4), (64, 4)):
+        return f"step_kernel_tmac<D3Q19,{elt},{m},{tx}x{ty}>"
+    return f"step_kernel<D3Q19,{elt},{m}>"
+
+
+def storage16_steps(rr, rb, rho, dev, stream, steps: int = 20):
+    """Step times of the same two lattices with FP16 storage of the shifted populations
+    (FP32 arithmetic), each on its autotuned tiling, with the fraction of the measured HBM
+    bandwidth at their algorithmic bytes (152 B/LU CG, 76 B/LU SC; not part of `value`)."""
+    import torch
+    from paper_2110_05197_gb300 import lbm, tune
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    peak, _ = hbm_peak()
+    out = {"bytes_per_lu": {"cg": 2 * 19 * 2 * 2, "sc": 19 * 2 * 2}}
+    for name, kw, fields in (("cg", cg_kw(), (rr, rb)), ("sc", sc_kw(), (rho,))):
+        lat = lbm.Lattice(lbm.Params(precision=lbm.FP16, **kw), stream=stream)
+        lat.init(*(t(f) for f in fields))
+        best, _ = tune.autotune(lat)
+        lat.step(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        gbs = out["bytes_per_lu"][name] * N3 ** 3 / (ms / 1e3) / 1e9
+        out[name] = {"step_ms": ms, "mlups": N3 ** 3 / (ms / 1e3) / 1e6, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "tiling": list(best), "kernel": kernel_label(name, lbm.FP16, best),
+                     "status": lbm.status_string(lat.totals()[1])}
+        lat.close()
+    return out
+
+
 def in_place_steps(rr, rb, rho, dev, stream, steps: int = 20):
     """Step times of the same two lattices with in-place (AA) streaming: one population
     buffer, a field pass plus the step kernel per step (not part of `value`)."""
@@ -423,20 +468,13 @@ def run_ours(args):
     cg_avg, sc_avg = float(np.mean(cg_ms)), float(np.mean(sc_ms))
     value = job_mlups(n, 2, K, ws, total_ms / 1e3)
     peak, peak_kind = hbm_peak()
-    # 32 x 8, 32 x 4 and 64 x 4 tiles run the cluster TMA kernel on this 128^3 lattice
-    # (clusters of nx / tx <= 8 blocks), 32 x 16 tiles the ring kernel; the label names
-    # the tile, whose traffic differs
-    tx_ty = list(tiling["cg"][:2])
-    if tx_ty in ([32, 8], [32, 4], [64, 4]):
-        cg_kernel = f"step_kernel_tmac<D3Q19,float,CG,{tx_ty[0]}x{tx_ty[1]}>"
-    elif tx_ty == [32, 16]:
-        cg_kernel = "step_kernel_ring<D3Q19,float,CG,32x16>"
-    else:
-        cg_kernel = "step_kernel<D3Q19,float,CG>"
+    cg_kernel = kernel_label("cg", lbm.FP32, tiling["cg"])
+    sc_kernel = kernel_label("sc", lbm.FP32, tiling["sc"])
     achieved = BYTES_PER_LU["cg"] * n / (cg_avg / 1e3) / 1e9
     tot_cg, rc_cg = cg.totals()
     tot_sc, rc_sc = sc.totals()
     in_place = in_place_steps(rr, rb, rho, dev, stream)
+    storage16 = storage16_steps(rr, rb, rho, dev, stream)
     multirange = multirange_steps(dev, stream)
 
     # end to end through the public API with pinned host buffers: init from host fields,
@@ -475,13 +513,16 @@ def run_ours(args):
                          "kernel": cg_kernel,
                          "bytes_per_lu": BYTES_PER_LU["cg"], "peak_kind": peak_kind,
                          "sc": {"achieved": BYTES_PER_LU["sc"] * n / (sc_avg / 1e3) / 1e9,
-                                "frac": BYTES_PER_LU["sc"] * n / (sc_avg / 1e3) / 1e9 / peak}},
+                                "frac": BYTES_PER_LU["sc"] * n / (sc_avg / 1e3) / 1e9 / peak,
+                                "kernel": sc_kernel, "bytes_per_lu": BYTES_PER_LU["sc"],
+                                "traffic": profiled_traffic(sc_kernel)}},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                     "request": f"init from pinned host fields + {K} CG and {K} SC steps + densities/totals to host"},
             "gpu_launches": launches,
             "tiling": tiling,
             "in_place": in_place,
+            "fp16_storage": storage16,
             "multirange": multirange,
             "status": {"cg": lbm.status_string(rc_cg), "sc": lbm.status_string(rc_sc),
                        "cg_mass_r": tot_cg["mass_r"], "sc_mass": tot_sc["mass_r"]},

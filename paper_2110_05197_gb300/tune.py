@@ -51,8 +51,10 @@ def time_steps(lat: "lbm.Lattice", steps: int) -> float:
     return a.elapsed_time(b) / steps
 
 
-def autotune(lat: "lbm.Lattice", candidates=None, steps: int = 3, use_cache: bool = True):
-    """Pick the fastest tiling for `lat` (state restored afterwards).  Returns
+def autotune(lat: "lbm.Lattice", candidates=None, steps: int = 10, trials: int = 2, use_cache: bool = True):
+    """Pick the fastest tiling for `lat` (state restored afterwards): each candidate is
+    timed `trials` times over `steps` steps and keeps its best time, so that run-to-run
+    noise of a few per cent does not flip close picks.  Returns
     (best tiling, {tiling: ms per step})."""
     key = shape_key(lat)
     if use_cache and key in _cache:
@@ -68,7 +70,7 @@ def autotune(lat: "lbm.Lattice", candidates=None, steps: int = 3, use_cache: boo
             continue
         lat.load_state(state, solid)
         lat.step(1)  # warm (first launch of a variant sets its shared-memory attribute)
-        timings[t] = time_steps(lat, steps)
+        timings[t] = min(time_steps(lat, steps) for _ in range(trials))
     best = min(timings, key=timings.get)
     lat.set_tiling(*best)
     lat.load_state(state, solid)
