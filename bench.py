@@ -219,25 +219,30 @@ def oracle_sample_mlups(steps: int, nz: int = 16, threads: int | None = None, bu
 
 
 def serving_sweep(n_req: int, seed: int = 5):
-    """Continuous-batching sweep (stability-map requests over 2D 256^2 and 32^3..96^3 grids,
-    CG or SC, 200-800 steps each = 1/25 of the 5k-20k of the full sweep).  First a closed
-    batch (every request at t = 0) through the plain FP32 one-at-a-time server measures its
+    """Continuous-batching sweep at the stated step range: stability-map requests over 2D
+    256^2 and 32^3..96^3 grids, CG or SC, 5000-20000 steps each (`n_req` of the 512
+    requests of the full sweep, seeded; nothing is extrapolated).  First a closed batch
+    (every request at t = 0) through the plain FP32 one-at-a-time server measures its
     service rate mu; then one Poisson trace at 1.2 mu is replayed through both servers."""
     import torch
     from paper_2110_05197_gb300 import lbm, serve
-    warm = serve.sweep(10, seed=1, steps=(5, 10), rate_hz=1e6)
-    serve.PlainServer(lbm.FP32).run(warm)           # tunes every grid shape once
+    # tune every grid shape and model once for both servers (tiling and batch chunk caches)
+    warm = [serve.Request(i, 0.0, g, m, kw, 5, 1) for i, (g, m, kw) in enumerate(
+        (g, m, dict(rho_r0=1.0, rho_b0=0.1, tau_r=1.0, tau_b=1.0, A=1e-2) if m == lbm.CG else
+         dict(G=-5.0, rho0_psi=1.0, tau_r=1.0)) for g in serve.GRIDS for m in (lbm.CG, lbm.SC_MP))]
+    serve.PlainServer(lbm.FP32).run(warm)
     serve.BatchServer(lbm.FP16, tick=100).run(warm)
     torch.cuda.synchronize()
-    closed = serve.sweep(n_req, seed=seed, steps=(200, 800), rate_hz=1e6)
-    out = {"requests": n_req, "steps": "U[200, 800] per request (1/25 of the 5k-20k sweep)",
+    steps = (5000, 20000)
+    closed = serve.sweep(n_req, seed=seed, steps=steps, rate_hz=1e6)
+    out = {"requests": n_req, "of_requests": 512, "steps": f"U[{steps[0]}, {steps[1]}] per request (the stated range)",
            "grids": [list(g) for g in serve.GRIDS], "precision": {"plain": "fp32", "batch": "fp16 storage"}}
     res_plain_closed = serve.PlainServer(lbm.FP32).run(closed)
     res_batch_closed = serve.BatchServer(lbm.FP16, tick=100).run(closed)
     pc, bc = serve.summary(res_plain_closed), serve.summary(res_batch_closed)
     out["closed_batch"] = {"plain_fp32": pc, "batch_fp16": bc, "sims_per_hour_ratio": bc["sims_per_hour"] / pc["sims_per_hour"]}
     mu = n_req / pc["makespan_s"]
-    trace = serve.sweep(n_req, seed=seed, steps=(200, 800), rate_hz=1.2 * mu)
+    trace = serve.sweep(n_req, seed=seed, steps=steps, rate_hz=1.2 * mu)
     plain_srv, batch_srv = serve.PlainServer(lbm.FP32), serve.BatchServer(lbm.FP16, tick=100)
     pp = serve.summary(plain_srv.run(trace))
     bb = serve.summary(batch_srv.run(trace))
@@ -549,7 +554,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiling", default=None, help="tx,ty,tz for both lattices (default: autotuned)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
-    ap.add_argument("--serving-requests", type=int, default=64)
+    ap.add_argument("--serving-requests", type=int, default=32,
+                    help="requests of the 512-request serving sweep to run at the full 5k-20k step range")
     ap.add_argument("--profile-only", default=None, choices=["cg", "sc", "mr", "aa_cg", "aa_sc"],
                     help="profiling runs: warm up and step only this lattice, print nothing")
     args = ap.parse_args()

@@ -166,16 +166,21 @@ lbm_status lbm_destroy(lbm_ctx* ctx);
 const char* lbm_status_string(lbm_status s);
 
 /* Tiling of the fused step kernel: a block owns tiles of tx * ty node columns (tx * ty <=
- * 256 and a multiple of 32) and marches them through z in z-chunks; work units are
- * (z-chunk, column) pairs taken chunk-major.  tz > 0: ceil(nz / tz) chunks of near-equal
- * length, one block per unit (tz must be 1 for D2Q9).  tz = 0: a persistent grid of as many
- * blocks as fit on the device looping over the units, with a chunk count chosen from that
- * block count.  Default 32 x 8 x 16.
+ * 256 and a multiple of 32, or one of the 512-node tiles below) and marches them through z
+ * in z-chunks; work units are (z-chunk, column) pairs taken chunk-major.  tz > 0:
+ * ceil(nz / tz) chunks of near-equal length, one block per unit (tz must be 1 for D2Q9).
+ * tz = 0: a persistent grid of as many blocks as fit on the device looping over the units,
+ * with a chunk count chosen from that block count.  Default 32 x 8 x 16.
  * D3Q19 lattices in FP32/FP16/BF16 with nx % 32 == 0 and ny % 8 == 0 run the TMA-staged
  * kernel when tx x ty is 32 x 8 (for nx <= 256 as clusters of nx / 32 blocks that exchange
  * the x-halo in distributed shared memory; the cluster kernel also takes 32 x 4, with two
  * blocks per SM, and 64 x 4 when nx % 64 == 0, in clusters of nx / 64), the generic kernel
- * otherwise.  Results are
+ * otherwise.  The ring kernel (the next plane's node state carried in registers, halo
+ * columns as asynchronous remote stores) takes the CG and SC-multiphase models without
+ * walls or the repulsion force: 32 x 16 and 64 x 8 tiles (one 512-thread block per SM;
+ * D3Q19 only; where it does not apply, the step runs 32 x 8 tiles), and 64 x 4 tiles
+ * where two of its blocks fit an SM (SC multiphase, or 16-bit storage), in clusters of
+ * nx / tx <= 8 blocks; it gives the cluster kernel's results bit for bit.  Results are
  * bitwise independent of the shape within each kernel; the kernels agree to a few ulps of
  * the stored populations (the compiler fuses multiply-adds differently).  LBM_EINVAL for
  * shapes outside those limits. */
@@ -184,7 +189,8 @@ lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t tx, int32_t ty, int32_t tz);
 /* ---- Batched stepping -------------------------------------------------------------
  * Many lattices (each an lbm_ctx) advance together: one persistent kernel launch per step
  * walks a device job table of all their work units (32 x 8 node columns times z-chunks
- * of <= 16 planes), so small lattices do not pay one launch each and fill the GPU
+ * of <= tz planes, tz the job's lbm_set_tiling value, 16 when it is 0), so small lattices
+ * do not pay one launch each and fill the GPU
  * together.  The per-node arithmetic is the generic step kernel's, so a lattice's result
  * is bitwise the same alone or in any mix (it may differ by a few ulps from a lattice
  * stepped with lbm_step_* on the TMA-staged kernel).  Jobs must be initialised, periodic

@@ -97,7 +97,10 @@ size_t workspace_layout(const lbm_params& p, lbm_ctx* c) {
   const size_t or0 = take((size_t)K * N * relt);
   const size_t or1 = aa ? or0 : take((size_t)K * N * relt);
   const size_t osol = take((size_t)N);
-  const size_t ostg = take((size_t)6 * N * sizeof(double));
+  // staging: rho_r, rho_b, momentum/velocity (3), then psi (SC multiphase) or the two
+  // multirange Psi_s in the compute type (a seventh row for FP64 storage)
+  const int stage_rows = (p.model == LBM_MODEL_SC_MR && p.precision == LBM_FP64) ? 7 : 6;
+  const size_t ostg = take((size_t)stage_rows * N * sizeof(double));
   const size_t opar = take((size_t)nblk * LBM_NTOTALS * sizeof(double));
   const size_t odia = take(sizeof(lbm_diag));
   const bool rep = p.model == LBM_MODEL_CG && p.rep_pi != 0.0;

@@ -247,29 +247,69 @@ __global__ void aa_gather_kernel(const S* __restrict__ f, S* __restrict__ out, c
   }
 }
 
+// x, y, z of node n (32-bit arithmetic whenever the node count allows it)
+__device__ __forceinline__ void node_xyz(long long n, const AuxParams& a, int& x, int& y, int& z) {
+  if (a.n < (1LL << 31)) {
+    const unsigned m = (unsigned)n, row = m / (unsigned)a.nx;
+    x = (int)(m - row * (unsigned)a.nx);
+    z = (int)(row / (unsigned)a.ny);
+    y = (int)(row - (unsigned)z * (unsigned)a.ny);
+  } else {
+    x = (int)(n % a.nx);
+    y = (int)((n / a.nx) % a.ny);
+    z = (int)(n / ((long long)a.nx * a.ny));
+  }
+}
+
+// One pass over the populations: the component densities rr, rb (FP64, as exact as FP64
+// summation), psi of Eq. pseudopotential (SC multiphase, FP64), the momentum
+// j = sum_k sum_i c_i f^k_i into jm [3][N] (FP64), and for the multirange model the
+// pseudopotentials Psi_s of both species in the step's compute type into mrpsi [2][N]
+// (read 92 times per node by the diagnostics' belt sums).
 template <class L, class S, class RT>
 __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__ f1, const RT* __restrict__ r0,
                                  const RT* __restrict__ r1, const lbm_diag* __restrict__ d, int cur,
                                  double* __restrict__ rr, double* __restrict__ rb, double* __restrict__ psi,
-                                 AuxParams a) {
+                                 double* __restrict__ jm, step_t<S>* __restrict__ mrpsi, AuxParams a) {
+  using C = step_t<S>;
   const int b = state_index(d, cur);
   const S* f = b ? f1 : f0;
   const RT* r = b ? r1 : r0;
   const bool odd = a.aa && (b & 1);
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+    // momentum summed exactly (ExactSum): the colours' momenta nearly cancel at
+    // interfaces, so rounding in the sum would show up in the reported u; the shift
+    // phi_i r is symmetric in c_i and carries no momentum: opposite pairs of the stored
+    // deviations
+    ExactSum<C> jx, jy, jz;
     for (int k = 0; k < 2; k++) {
       double s = 0.0;
       if (k < a.K) {
-        ExactSum<step_t<S>> acc{static_cast<step_t<S>>(r[(long long)k * a.n + m])};  // sum_i phi_i = 1
+        ExactSum<C> acc{static_cast<C>(r[(long long)k * a.n + m])};  // sum_i phi_i = 1
 #pragma unroll
         for (int i = 0; i < L::Q; i++)
-          acc.add(ld_s<S, step_t<S>>(f[aa_index_n<L>(k, i, m, a.nx, a.ny, a.nz, a.n, odd)]));
+          acc.add(ld_s<S, C>(f[aa_index_n<L>(k, i, m, a.nx, a.ny, a.nz, a.n, odd)]));
         s = acc.value();
+#pragma unroll
+        for (int q = 0; q < L::NP; q++) {
+          const C vp = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 1, m, a.nx, a.ny, a.nz, a.n, odd)]);
+          const C vm = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 2, m, a.nx, a.ny, a.nz, a.n, odd)]);
+          if (L::pcx(q)) { jx.add(L::pcx(q) > 0 ? vp : -vp); jx.add(L::pcx(q) > 0 ? -vm : vm); }
+          if (L::pcy(q)) { jy.add(L::pcy(q) > 0 ? vp : -vp); jy.add(L::pcy(q) > 0 ? -vm : vm); }
+          if (L::pcz(q)) { jz.add(L::pcz(q) > 0 ? vp : -vp); jz.add(L::pcz(q) > 0 ? -vm : vm); }
+        }
       }
       (k == 0 ? rr : rb)[m] = s;
       // Eq. pseudopotential, once per node (the force stencil reads it 18 times)
       if (k == 0 && a.model == LBM_MODEL_SC_MP) psi[m] = a.rho0 * (1.0 - exp(-s / a.rho0));
+      if (mrpsi) {  // Psi_s = rho_0 (1 - exp(-rho_s / rho_0)) in the compute type
+        const C c0 = C(a.rho0), ic0 = C(1.0 / a.rho0);
+        mrpsi[(long long)k * a.n + m] = c0 * (C(1) - exp(-C(s) * ic0));
+      }
     }
+    jm[m] = jx.value();
+    jm[a.n + m] = jy.value();
+    jm[2 * a.n + m] = jz.value();
   }
 }
 
@@ -310,57 +350,39 @@ __device__ void block_reduce(Acc& a) {
   }
 }
 
+// Per-node velocity and the block partials of the totals, from the staged densities and
+// momentum (densities_kernel): no population is read again.  u (force-shifted, Eq.
+// guoforce) may be written over jm (uo == jm): each node reads its own momentum first.
+// Slot 6 of the partials holds max |u|^2 (its square root is taken in the final pass).
 template <class L, class S, class RT>
-__global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict__ f0, const S* __restrict__ f1,
-                                                            const RT* __restrict__ r0, const RT* __restrict__ r1,
-                                                            const lbm_diag* __restrict__ d, int cur,
-                                                            const double* __restrict__ rr,
+__global__ void __launch_bounds__(kDiagThreads) diag_kernel(const double* __restrict__ rr,
                                                             const double* __restrict__ rb,
                                                             const double* __restrict__ psi,
-                                                            const uint8_t* __restrict__ solid, double* __restrict__ uo,
+                                                            const double* jm,
+                                                            const step_t<S>* __restrict__ mrpsi,
+                                                            const uint8_t* __restrict__ solid, double* uo,
                                                             double* __restrict__ partials, AuxParams a,
                                                             const step_t<S>* __restrict__ colour,
                                                             const step_t<S>* __restrict__ normals, RepParams rp) {
-  using C = step_t<S>;  // per-node arithmetic; the sums below are FP64
-  const int bsel = state_index(d, cur);
-  const S* f = bsel ? f1 : f0;
-  const RT* rref = bsel ? r1 : r0;
-  const bool odd = a.aa && (bsel & 1);
+  using C = step_t<S>;  // per-node arithmetic of the multirange belts; the sums below are FP64
   Acc acc;
   acc_init(acc);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
     const bool wall = solid && solid[n];
-    // momentum summed exactly (ExactSum): the colours' momenta nearly cancel at
-    // interfaces, so rounding in the sum would show up in the reported u
-    ExactSum<C> jx, jy, jz;
-    int bad = 0;
-    for (int k = 0; k < a.K; k++) {
-      const C rk = C(rref[(long long)k * a.n + n]);
-      if (!isfinite(rk)) bad = 1;
-      // the shift phi_i r is symmetric in c_i and carries no momentum: opposite pairs of
-      // the stored deviations
-#pragma unroll
-      for (int q = 0; q < L::NP; q++) {
-        const C vp = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 1, n, a.nx, a.ny, a.nz, a.n, odd)]);
-        const C vm = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 2, n, a.nx, a.ny, a.nz, a.n, odd)]);
-        if (!isfinite(vp) || !isfinite(vm)) bad = 1;
-        if (L::pcx(q)) { jx.add(L::pcx(q) > 0 ? vp : -vp); jx.add(L::pcx(q) > 0 ? -vm : vm); }
-        if (L::pcy(q)) { jy.add(L::pcy(q) > 0 ? vp : -vp); jy.add(L::pcy(q) > 0 ? -vm : vm); }
-        if (L::pcz(q)) { jz.add(L::pcz(q) > 0 ? vp : -vp); jz.add(L::pcz(q) > 0 ? -vm : vm); }
-      }
-      if (!isfinite(ld_s<S, C>(f[(long long)(k * L::Q) * a.n + n]))) bad = 1;
-    }
-    const double j[3] = {jx.value(), jy.value(), jz.value()};
+    const double j[3] = {jm[n], jm[a.n + n], jm[2 * a.n + n]};
     const double r = rr[n], b = rb[n], rho = r + b;
+    const int bad = !(isfinite(r) && isfinite(b) && isfinite(j[0]) && isfinite(j[1]) && isfinite(j[2]));
     double F[3] = {a.body[0], a.body[1], a.body[2]};
     if (!wall && a.model == LBM_MODEL_CG && normals) {
-      const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+      int x, y, z;
+      node_xyz(n, a, x, y, z);
       C Fr[3];
       rep_force<L, C>(normals, colour, solid, x, y, z, rp, Fr);  // the step's own precision
       for (int dd = 0; dd < 3; dd++) F[dd] += double(Fr[dd]);
     }
     if (!wall && a.model != LBM_MODEL_CG) {
-      const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+      int x, y, z;
+      node_xyz(n, a, x, y, z);
       // sum_i w_i phi(x + c_i) c_i as opposite-pair differences in FP64 (the force is a
       // small difference of O(1) values)
       double s1[3] = {0.0, 0.0, 0.0}, s2[3] = {0.0, 0.0, 0.0};
@@ -391,36 +413,45 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
       }
       if (a.model == LBM_MODEL_SC_MR) {
         // self forces of Eqs. doublebeltattractiveforce / doublebeltrepulsionforce with
-        // Psi_s = rho_0 (1 - exp(-rho_s / rho_0)), evaluated in the step's compute type C
-        // (FP64 only for FP64 storage: 92 exponentials per node); a wall neighbour takes
-        // the centre value
+        // the staged Psi_s, summed in the step's compute type C as the step kernel sums
+        // them (FP64 only for FP64 storage); a wall neighbour takes the centre value
+        const bool small = a.n < (1LL << 31);
         for (int sp = 0; sp < 2; sp++) {
-          const double* rs = sp ? rb : rr;
-          const C r0 = C(a.rho0), ir0 = C(1.0 / a.rho0);
-          const double pc = double(r0 * (C(1) - exp(-C(rs[n]) * ir0)));
-          auto psi_at = [&](int dx, int dy, int dz) {
-            const long long m = nb_index(x, y, z, dx, dy, dz, a.nx, a.ny, a.nz);
-            return (solid && solid[m]) ? pc : double(r0 * (C(1) - exp(-C(rs[m]) * ir0)));
+          const C* ps = mrpsi + (long long)sp * a.n;
+          const C pc = ps[n];
+          auto psi_at = [&](int dx, int dy, int dz) -> C {
+            int X = x + dx, Y = y + dy, Z = z + dz;
+            X = X < 0 ? X + a.nx : (X >= a.nx ? X - a.nx : X);
+            Y = Y < 0 ? Y + a.ny : (Y >= a.ny ? Y - a.ny : Y);
+            Z = Z < 0 ? Z + a.nz : (Z >= a.nz ? Z - a.nz : Z);
+            const long long m = small ? (long long)(unsigned)(X + a.nx * (Y + a.ny * Z))
+                                      : X + (long long)a.nx * (Y + (long long)a.ny * Z);
+            return (solid && solid[m]) ? pc : ps[m];
           };
-          double att[3] = {0.0, 0.0, 0.0}, rep[3] = {0.0, 0.0, 0.0};
+          C att[3] = {C(0), C(0), C(0)}, rep[3] = {C(0), C(0), C(0)};
+#pragma unroll
           for (int q = 0; q < L::NP; q++) {
-            const double d = L::w(L::pgrp(q)) * (psi_at(L::pcx(q), L::pcy(q), L::pcz(q)) -
-                                                 psi_at(-L::pcx(q), -L::pcy(q), -L::pcz(q)));
-            att[0] += L::pcx(q) * d;
-            att[1] += L::pcy(q) * d;
-            att[2] += L::pcz(q) * d;
+            const C d = C(L::w(L::pgrp(q))) * (psi_at(L::pcx(q), L::pcy(q), L::pcz(q)) -
+                                               psi_at(-L::pcx(q), -L::pcy(q), -L::pcz(q)));
+            if (L::pcx(q)) att[0] += L::pcx(q) * d;
+            if (L::pcy(q)) att[1] += L::pcy(q) * d;
+            if (L::pcz(q)) att[2] += L::pcz(q) * d;
           }
+#pragma unroll
           for (int dz = 0; dz <= 2; dz++)
+#pragma unroll
             for (int dy = -2; dy <= 2; dy++)
+#pragma unroll
               for (int dx = -2; dx <= 2; dx++) {
                 const int r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 == 0 || mr_weight(r2) == 0.0 || !(dz > 0 || dy > 0 || (dy == 0 && dx > 0))) continue;
-                const double d = mr_weight(r2) * (psi_at(dx, dy, dz) - psi_at(-dx, -dy, -dz));
-                rep[0] += dx * d;
-                rep[1] += dy * d;
-                rep[2] += dz * d;
+                if (r2 == 0 || r2 > 8 || mr_weight(r2) == 0.0 || !(dz > 0 || dy > 0 || (dy == 0 && dx > 0))) continue;
+                const C d = C(mr_weight(r2)) * (psi_at(dx, dy, dz) - psi_at(-dx, -dy, -dz));
+                if (dx) rep[0] += C(dx) * d;
+                if (dy) rep[1] += C(dy) * d;
+                if (dz) rep[2] += C(dz) * d;
               }
-          for (int dd = 0; dd < 3; dd++) F[dd] += -a.Ga[sp] * pc * att[dd] - a.Gr[sp] * pc * rep[dd];
+          for (int dd = 0; dd < 3; dd++)
+            F[dd] += -a.Ga[sp] * double(pc) * double(att[dd]) - a.Gr[sp] * double(pc) * double(rep[dd]);
         }
       }
     }
@@ -442,7 +473,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const S* __restrict_
     acc.v[3] += j[1];
     acc.v[4] += j[2];
     acc.v[5] += 0.5 * rho * uu;
-    acc.v[6] = fmax(acc.v[6], sqrt(uu));
+    acc.v[6] = fmax(acc.v[6], uu);
     acc.v[7] += bad;
     acc.v[8] = fmin(acc.v[8], r);
     acc.v[9] = fmin(acc.v[9], b);
@@ -463,6 +494,7 @@ __global__ void __launch_bounds__(kDiagThreads) finalize_kernel(const double* __
   }
   block_reduce(acc);
   if (threadIdx.x == 0) {
+    acc.v[6] = sqrt(acc.v[6]);  // max |u| from max |u|^2 (sqrt is monotonic and correctly rounded)
     int st = 0;
     if (acc.v[7] > 0 || !isfinite(acc.v[0]) || !isfinite(acc.v[1])) st |= 1;
     if (acc.v[8] < -a.neg_tol || acc.v[9] < -a.neg_tol) st |= 2;
@@ -528,9 +560,11 @@ cudaError_t diag_t(lbm_ctx* c, double* uo) {
   const RT* r1 = static_cast<const RT*>(c->r[1]);
   double* rr = c->stage;
   double* rb = c->stage + c->N;
-  double* psi = c->stage + 5 * c->N;
+  double* jm = c->stage + 2 * c->N;   // momentum, then (if requested here) the velocity
+  double* psi = c->stage + 5 * c->N;  // SC multiphase psi (FP64), or the multirange Psi_s
+  step_t<S>* mrpsi = c->p.model == LBM_MODEL_SC_MR ? reinterpret_cast<step_t<S>*>(psi) : nullptr;
   densities_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(f0, f1, r0, r1, c->diag, c->cur, rr,
-                                                                               rb, psi, a);
+                                                                               rb, psi, jm, mrpsi, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (c->rep) {
@@ -538,7 +572,7 @@ cudaError_t diag_t(lbm_ctx* c, double* uo) {
     if (e != cudaSuccess) return e;
   }
   diag_kernel<L, S, RT><<<c->nblk_diag, kDiagThreads, 0, c->stream>>>(
-      f0, f1, r0, r1, c->diag, c->cur, rr, rb, psi, c->has_walls ? c->solid : nullptr, uo, c->partials, a,
+      rr, rb, psi, jm, mrpsi, c->has_walls ? c->solid : nullptr, uo, c->partials, a,
       static_cast<const step_t<S>*>(c->colour), static_cast<const step_t<S>*>(c->normals), rep_params(c));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

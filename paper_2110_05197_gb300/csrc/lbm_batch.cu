@@ -48,7 +48,7 @@ lbm_status bfail(lbm_batch* b, cudaError_t e) {
 
 int units_of(const lbm_ctx* c) {
   const int ncol = ((c->p.nx + lbm::kBatchTX - 1) / lbm::kBatchTX) * ((c->p.ny + lbm::kBatchTY - 1) / lbm::kBatchTY);
-  const int nch = c->p.lattice == LBM_D3Q19 ? (c->p.nz + lbm::kBatchChunk - 1) / lbm::kBatchChunk : 1;
+  const int nch = c->p.lattice == LBM_D3Q19 ? (c->p.nz + lbm::batch_chunk(c) - 1) / lbm::batch_chunk(c) : 1;
   return ncol * nch;
 }
 

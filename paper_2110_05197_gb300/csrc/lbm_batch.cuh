@@ -1,7 +1,8 @@
 // Batched stepping: many lattices advance in one persistent launch driven by a job table.
 //
 // Every lattice of a batch (a "job": one lbm_ctx) is cut into work units of 32 x 8 node
-// columns and z-chunks of at most 16 planes; the unit list of all jobs sits in device
+// columns and z-chunks of at most tz planes (the job's tiling; 16 by default); the unit
+// list of all jobs sits in device
 // memory beside the job descriptors (array pointers, StepParams, the buffer pair holding
 // the state, the steps the job still takes).  One launch advances every job by one step:
 // a persistent grid walks the unit list with a stride, loads the unit's job descriptor
@@ -21,7 +22,12 @@ struct lbm_batch;
 namespace lbm {
 
 constexpr int kBatchTX = 32, kBatchTY = 8;  // block shape of the batched kernel
-constexpr int kBatchChunk = 16;            // z planes per work unit (3-D lattices)
+constexpr int kBatchChunk = 16;            // default z planes per work unit (3-D lattices)
+
+// z planes per work unit of a job: the context's own tz (lbm_set_tiling) when it is set,
+// else kBatchChunk.  Shorter chunks give small lattices more units (more of the GPU) at
+// the price of two halo planes per unit.
+inline int batch_chunk(const lbm_ctx* c) { return c->tz > 0 ? c->tz : kBatchChunk; }
 
 template <class T, class S, class RT>
 struct BatchJob {
@@ -129,7 +135,7 @@ void batch_fill_job(const lbm_ctx* c, int nsteps, void* dst) {
   j.p = make_step_params<T>(c);
   j.p.ncx = (c->p.nx + kBatchTX - 1) / kBatchTX;
   j.p.ncol = j.p.ncx * ((c->p.ny + kBatchTY - 1) / kBatchTY);
-  j.p.nchunks = c->p.lattice == LBM_D3Q19 ? (c->p.nz + kBatchChunk - 1) / kBatchChunk : 1;
+  j.p.nchunks = c->p.lattice == LBM_D3Q19 ? (c->p.nz + batch_chunk(c) - 1) / batch_chunk(c) : 1;
   j.p.nblk = 0;  // unused: the batch's unit list replaces the per-lattice partition
   *static_cast<BatchJob<T, S, RT>*>(dst) = j;
 }

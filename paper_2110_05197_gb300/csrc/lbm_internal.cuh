@@ -35,7 +35,9 @@ struct lbm_ctx {
                          // layout parity of the state (lbm_step_aa.cuh)
   uint8_t* solid;        // [N] wall mask (all zero without walls)
   bool has_walls;
-  double* stage;         // [6][N] FP64 staging: rho_r, rho_b, u_x, u_y, u_z, psi (SC multiphase);
+  double* stage;         // [6][N] FP64 staging ([7][N] for the multirange model in FP64):
+                         // rho_r, rho_b, momentum then u (x, y, z), psi (SC multiphase) or
+                         // the multirange Psi_s in the compute type;
                          // in-place streaming also uses it for the step's field pass
   double* partials;      // [nblk_diag][LBM_NTOTALS]
   int nblk_diag;

@@ -90,6 +90,32 @@ def capsule(nx, ny, nz, radius=8.0, length=None):
     return (x - cx) ** 2 + (y - cy) ** 2 + dz ** 2 <= radius ** 2
 
 
+def capsule_distance(nx, ny, nz, radius=8.0, length=None):
+    """Signed distance to the surface of ``capsule`` (negative inside)."""
+    x, y, z = grid(nx, ny, nz)
+    if length is None:
+        length = 40.0 * 2.0 * radius
+    cx, cy, cz = (nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0
+    half = length / 2.0 - radius
+    dz = np.clip(np.abs(z - cz) - half, 0.0, None)
+    return np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + dz ** 2) - radius
+
+
+def diffuse_two_fluid(distance: np.ndarray, rho_in: float, rho_out: float, width: float,
+                      noise: float = 0.0, seed: int = 0):
+    """Interface of finite width instead of a step: component R = rho_in (1 - tanh(d/w))/2,
+    component B = rho_out (1 + tanh(d/w))/2 at signed distance d (negative inside);
+    ``noise`` as in two_fluid."""
+    n = distance.size
+    t = np.tanh(distance / width)
+    rr = rho_in * 0.5 * (1.0 - t)
+    rb = rho_out * 0.5 * (1.0 + t)
+    if noise:
+        rr = rr * (1.0 + noise * uniform_pm1(seed, n, 0))
+        rb = rb * (1.0 + noise * uniform_pm1(seed, n, 1))
+    return rr, rb
+
+
 def slab(nx, ny, nz, lo, hi, axis=0):
     """Indicator lo <= coordinate < hi along ``axis`` (flat interfaces, layered flows)."""
     c = grid(nx, ny, nz)[axis]

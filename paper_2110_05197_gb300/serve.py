@@ -8,13 +8,14 @@ Two servers answer the same request trace:
 * ``BatchServer`` admits requests as they arrive while the device memory budget and the
   batch table have room, keeps their lattices resident, and advances all of them together:
   lattices up to ``batch_max_nodes`` nodes share one persistent batched launch per step
-  (lbm_batch_*, replayed as a CUDA graph per tick of ``tick`` steps), larger ones are
-  stepped with their own tuned kernel on a second stream so their work overlaps the batch,
-  first come first served (they share that stream, and interleaving them would only make
-  each finish later).  The two streams run independently: an event marks each one's work
-  in flight, and the host launches the next tick or job as soon as one completes.
-  A finished request's moments are read and its memory is released as soon as its work
-  completes; new small requests join at the next tick.
+  (lbm_batch_*, replayed as a CUDA graph per tick of ``tick`` steps; each job's z-chunk
+  length picked by the batch autotuner, tune.batch_chunk), larger ones are stepped with
+  their own tuned kernel on ``big_streams`` further streams, one job per stream, in ticks
+  of ``big_tick`` steps, so that several large lattices and the batch overlap on the
+  device.  Every stream runs independently: an event marks its work in flight, and the
+  host launches the next tick or job as soon as one completes.  A finished request's
+  moments are read and its memory is released as soon as its work completes; new requests
+  join at the next tick of their stream.
 
 Results are the FP64 totals (lbm_moments) and the component densities; the latency of a
 request is completion minus arrival on a common wall clock.  The physics of a job does
@@ -158,7 +159,7 @@ class BatchServer:
 
     def __init__(self, precision: int = lbm.FP16, budget_bytes: int = 8 << 30, tick: int = 100,
                  max_jobs: int = 256, max_units: int = 1 << 16, batch_max_nodes: int = 120_000,
-                 graph: bool = True, keep_fields: bool = False):
+                 graph: bool = True, keep_fields: bool = False, big_streams: int = 4, big_tick: int = 500):
         self.precision = precision
         self.budget = budget_bytes
         self.tick = tick
@@ -167,25 +168,27 @@ class BatchServer:
         self.batch_max_nodes = batch_max_nodes
         self.graph = graph
         self.keep_fields = keep_fields
+        self.big_streams = big_streams
+        self.big_tick = big_tick
         self.launches = 0
         self.peak_bytes = 0
         self.peak_jobs = 0
 
     def run(self, requests, t0=None):
         import torch
-        small_stream, big_stream = torch.cuda.Stream(), torch.cuda.Stream()
+        small_stream = torch.cuda.Stream()
+        slots = [dict(stream=torch.cuda.Stream(), ev=None, job=None) for _ in range(self.big_streams)]
         batch = lbm.Batch(self.precision, self.max_jobs, self.max_units, stream=small_stream)
         t0 = time.perf_counter() if t0 is None else t0
         clock = lambda: time.perf_counter() - t0
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        smalls, bigs = [], []  # active jobs (dicts: req, lat, left, start, bytes, small, units)
+        smalls, bigs_waiting = [], deque()  # active jobs (dicts: req, lat, left, start, bytes, small, units)
+        n_big_active = 0
         out = []
         used = 0
         units_used = 0
         dirty = False
-        # each stream runs independently: an event marks the end of its work in flight
         small_ev, small_running = None, []
-        big_ev, big_running = None, None
 
         def finish(a):
             nonlocal used, units_used
@@ -194,7 +197,7 @@ class BatchServer:
             used -= a["bytes"]
             units_used -= a["units"]
 
-        while pending or smalls or bigs:
+        while pending or smalls or bigs_waiting or n_big_active:
             now = clock()
             # admission: arrived requests, FIFO, while memory and table room remain
             while pending and pending[0].arrival <= now:
@@ -202,22 +205,27 @@ class BatchServer:
                 p = req.params(self.precision)
                 need = lbm.workspace_bytes(p)
                 small = req.nodes <= self.batch_max_nodes
-                nu = 0
-                if small:
-                    nx, ny, nz = req.grid
-                    nu = math.ceil(nx / 32) * math.ceil(ny / 8) * (math.ceil(nz / 16) if nz > 1 else 1)
-                if used + need > self.budget or (small and (units_used + nu > self.max_units or
-                                                            len(smalls) >= self.max_jobs)):
+                if used + need > self.budget or (small and len(smalls) >= self.max_jobs):
                     break
-                pending.popleft()
-                lat = _new_lattice(req, self.precision, small_stream if small else big_stream, tuned=not small)
-                job = dict(req=req, lat=lat, left=req.steps, start=now, bytes=need, small=small, units=nu)
-                (smalls if small else bigs).append(job)
+                if small:
+                    # the batch stream: its job's z-chunk from the batch autotuner
+                    lat = _new_lattice(req, self.precision, small_stream, tuned=False)
+                    lat.set_tiling(32, 8, tune.batch_chunk(req.params(self.precision)))
+                    nu = lbm.Batch.units(lat)
+                    if units_used + nu > self.max_units:
+                        lat.close()
+                        break
+                    pending.popleft()
+                    smalls.append(dict(req=req, lat=lat, left=req.steps, start=now, bytes=need, small=True, units=nu))
+                    units_used += nu
+                    dirty = True
+                else:
+                    pending.popleft()
+                    bigs_waiting.append(dict(req=req, lat=None, left=req.steps, start=now, bytes=need, small=False,
+                                             units=0))
                 used += need
-                units_used += nu
-                dirty = dirty or small
             self.peak_bytes = max(self.peak_bytes, used)
-            self.peak_jobs = max(self.peak_jobs, len(smalls) + len(bigs))
+            self.peak_jobs = max(self.peak_jobs, len(smalls) + n_big_active + len(bigs_waiting))
             progressed = False
             # small lattices: one batched launch per step, ticks of `tick` steps as a graph;
             # the job list changes only between ticks
@@ -239,25 +247,34 @@ class BatchServer:
                     small_ev = torch.cuda.Event()
                     small_ev.record(small_stream)
                     small_running = list(smalls)
-            # large lattices share the second stream, first come first served: the oldest
-            # runs all its steps (interleaving them would only make each finish later)
-            if big_ev is None or big_ev.query():
-                if big_ev is not None:
-                    bigs.remove(big_running)
-                    finish(big_running)
-                    big_ev, big_running = None, None
+            # large lattices: one job per stream slot, ticks of `big_tick` steps
+            for sl in slots:
+                if sl["ev"] is not None and not sl["ev"].query():
+                    continue
+                a = sl["job"]
+                if a is not None and a["left"] == 0:
+                    finish(a)
+                    sl["job"], a = None, None
+                    n_big_active -= 1
                     progressed = True
-                if bigs:
-                    a = bigs[0]
+                if a is None and bigs_waiting:
+                    a = bigs_waiting.popleft()
+                    a["lat"] = _new_lattice(a["req"], self.precision, sl["stream"], tuned=True)
+                    sl["job"] = a
+                    n_big_active += 1
+                if a is not None:
+                    k = min(self.big_tick, a["left"])
                     l0 = a["lat"].launch_count()
-                    a["lat"].step(a["left"])
+                    a["lat"].step(k)
                     self.launches += a["lat"].launch_count() - l0
-                    a["left"] = 0
-                    big_ev = torch.cuda.Event()
-                    big_ev.record(big_stream)
-                    big_running = a
+                    a["left"] -= k
+                    sl["ev"] = torch.cuda.Event()
+                    sl["ev"].record(sl["stream"])
+                    progressed = True
+                else:
+                    sl["ev"] = None
             if not progressed:
-                if small_ev is None and big_ev is None and pending:
+                if small_ev is None and not n_big_active and pending:
                     time.sleep(min(1e-3, max(0.0, pending[0].arrival - clock())))
                 else:
                     time.sleep(2e-5)

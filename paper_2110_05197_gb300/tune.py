@@ -17,7 +17,8 @@ from . import lbm
 # tz = 0 selects the persistent grid (equal shares of all tile-planes per resident block)
 CANDIDATES_3D = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (16, 8, 0), (128, 2, 0),
                  (32, 8, 16), (32, 8, 22), (32, 8, 32), (32, 4, 16), (64, 4, 16),
-                 (32, 16, 0), (64, 8, 0)]  # the last two: the ring kernel where it applies
+                 (32, 16, 0), (64, 8, 0),   # the ring kernel where it applies
+                 (32, 8, 4), (32, 4, 4), (64, 4, 4)]  # short chunks: more units on small lattices
 CANDIDATES_2D = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (128, 2, 0), (32, 8, 1), (32, 4, 1), (64, 4, 1), (128, 2, 1)]
 
 _cache: dict = {}
@@ -76,3 +77,53 @@ def autotune(lat: "lbm.Lattice", candidates=None, steps: int = 10, trials: int =
     lat.load_state(state, solid)
     _cache[key] = (best, timings)
     return best, timings
+
+
+_batch_cache: dict = {}
+BATCH_CHUNKS = (4, 8, 16)
+
+
+def batch_chunk(p: "lbm.Params", copies: int = 8, steps: int = 20) -> int:
+    """z planes per work unit for a lattice of these parameters in the batched launch
+    (lbm_batch_*): times `copies` lattices of the shape, batched, for each chunk length in
+    BATCH_CHUNKS and keeps the fastest (cached per shape, model and precision).  Shorter
+    chunks give a small lattice more units; each unit also stages two halo planes.  The
+    chunk length does not change results: every node is computed the same way."""
+    import numpy as np
+    key = (p.lattice, p.model, p.precision, p.nx, p.ny, p.nz)
+    if p.lattice != lbm.D3Q19:
+        return 1
+    if key in _batch_cache:
+        return _batch_cache[key]
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rng = np.random.default_rng(0)
+    best, best_ms = BATCH_CHUNKS[-1], float("inf")
+    for tz in BATCH_CHUNKS:
+        if tz > p.nz:
+            continue
+        lats = []
+        for _ in range(copies):
+            lat = lbm.Lattice(p, stream=stream)
+            rr = torch.as_tensor(1.0 + 0.01 * rng.standard_normal(p.n), device=dev)
+            rb = None if p.model == lbm.SC_MP else torch.as_tensor(0.1 + 0.001 * rng.standard_normal(p.n), device=dev)
+            with torch.cuda.stream(stream):
+                lat.init(rr, rb)
+            lat.set_tiling(32, 8, tz)
+            lats.append(lat)
+        b = lbm.Batch(p.precision, copies, 1 << 16, stream=stream)
+        b.set(lats, [10 ** 6] * copies)
+        b.step(steps)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        b.step(steps)
+        e.record(stream)
+        e.synchronize()
+        ms = a.elapsed_time(e)
+        b.close()
+        for lat in lats:
+            lat.close()
+        if ms < best_ms:
+            best, best_ms = tz, ms
+    _batch_cache[key] = best
+    return best

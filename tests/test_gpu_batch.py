@@ -105,3 +105,25 @@ def test_serving_batch_matches_plain(lbm):
         assert err < 5e-3 and dm < 1e-4
     s = serve.summary(list(batch.values()))
     assert s["p99_s"] >= s["p50_s"] > 0 and s["sims_per_hour"] > 0
+
+
+def test_batch_chunk_length_does_not_change_results(lbm):
+    """A job's z-chunk length in the batched launch (its tiling's tz, picked by the batch
+    autotuner) changes only the work partition: the state is bitwise the same."""
+    import torch
+    from paper_2110_05197_gb300 import tune
+    outs = []
+    for tz in (4, 16, 0):
+        cases, lats = _mix(lbm, lbm.FP16)
+        for lat in lats[:4]:          # the 3-D lattices
+            lat.set_tiling(32, 8, tz)
+        b = lbm.Batch(lbm.FP16, 16, 4096, stream=lats[0].stream)
+        b.set(lats, [20] * len(lats))
+        b.step(20)
+        torch.cuda.synchronize()
+        outs.append([lat.pops().cpu().numpy() for lat in lats])
+    for other in outs[1:]:
+        for a, b_ in zip(outs[0], other):
+            assert np.array_equal(a, b_)
+    p = lbm.Params(lattice=lbm.D3Q19, model=lbm.CG, precision=lbm.FP16, nx=32, ny=32, nz=32, rho_b0=0.1)
+    assert tune.batch_chunk(p) in tune.BATCH_CHUNKS

@@ -368,3 +368,39 @@ def test_ring_kernel(orc, lbm, name, precision):
     for m in ("mass_r", "mass_b"):
         if t0[m] > 0:
             assert abs(tot[m] - t0[m]) <= 1e-6 * t0[m]
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_full_size_100_steps_benchmark_tiling(orc, lbm, model):
+    """The 128^3 droplet of the benchmark in its tuned launch shape (64 x 4 tiles: the
+    cluster TMA kernel for FP32 CG, the ring kernel for FP32 SC multiphase): 100 FP32 steps
+    against 100 oracle steps, densities element by element and velocities at the FP32
+    bounds, mass drift <= 1e-6."""
+    n = 128
+    if model == 0:
+        rr, rb = C.inputs.two_fluid(C.inputs.ellipsoid(n, n, n, (24, 20, 20)), 1.0, 0.1, 0.01, 2)
+        kw = dict(lattice=1, model=0, nx=n, ny=n, nz=n, rho_r0=1.0, rho_b0=0.1, A=5e-3)
+    else:
+        ins = C.inputs.ellipsoid(n, n, n, (24, 20, 20))
+        rr = np.where(ins, C.SC_LIQ, C.SC_GAS) * (1 + 0.01 * C.inputs.uniform_pm1(2, n ** 3))
+        rb = None
+        kw = dict(lattice=1, model=1, nx=n, ny=n, nz=n, G=-5.0, rho0_psi=1.0)
+    case = C.Case("full", kw, rr, rb)
+    s = C.oracle_sim(orc, case)
+    lat = C.gpu_lattice(lbm, case, lbm.FP32)
+    lat.set_tiling(64, 4, 0)
+    t0, _ = lat.totals()
+    s.step(100)
+    lat.step(100)
+    grr, grb, u, tot, rc = lat.moments(device=False)
+    orr, orb, ou, _ = s.moments()
+    assert rc == lbm.OK
+    scale = max(orr.max(), orb.max())
+    er = np.max(np.abs(grr - orr) / np.maximum(np.abs(orr), 1e-3 * scale))
+    eb = np.max(np.abs(grb - orb) / np.maximum(np.abs(orb), 1e-3 * scale))
+    eu2 = np.linalg.norm(u - ou) / np.linalg.norm(ou)
+    eu = np.max(np.abs(u - ou)) / np.max(np.abs(ou))
+    dm = max(abs(tot[m] - t0[m]) / t0[m] for m in ("mass_r", "mass_b") if t0[m] > 0)
+    print(f"128^3 model {model} FP32 64x4 after 100 steps: rho {er:.2e}/{eb:.2e}, u L2 {eu2:.2e}, max {eu:.2e}, "
+          f"mass drift {dm:.2e}")
+    assert er < 1e-5 and eb < 1e-5 and eu2 < 1e-5 and eu < 3e-5 and dm < 1e-6
