@@ -299,6 +299,41 @@ def storage16_steps(rr, rb, rho, dev, stream, steps: int = 20):
     return out
 
 
+def emulsion_steps(dev, stream, steps: int = 10):
+    """Step times of the dense emulsion with the CG repulsion force (256^3 periodic, 200
+    droplets of radius 10 +- 2, Table emulsionParams: rho 1.36, A 0.0518, Pi 0.012, chi 2),
+    FP32 and FP16 storage, autotuned; MLUPS and the fraction of the measured HBM bandwidth
+    at the algorithmic bytes (304 / 152 B/LU; the repulsion pre-pass's colour and normal
+    fields are implementation traffic).  Not part of `value`."""
+    import torch
+    from paper_2110_05197_gb300 import lbm, tune
+    n = 256
+    ins, _ = inputs.emulsion(n, n, n, count=200, r_mean=10.0, r_spread=2.0, gap=3.0, seed=4)
+    rr, rb = inputs.two_fluid(ins, 1.36, 1.36, 0.01, 5)
+    kw = dict(lattice=1, model=0, nx=n, ny=n, nz=n, rho_r0=1.36, rho_b0=1.36, A=0.0518, rep_pi=0.012, rep_chi=2.0,
+              grad_eps=1e-4)
+    peak, _ = hbm_peak()
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    out = {"workload": "CG dense emulsion with the repulsion force, 256^3, 200 droplets", "steps": steps}
+    for name, prec, bpl in (("fp32", lbm.FP32, 304), ("fp16", lbm.FP16, 152)):
+        lat = lbm.Lattice(lbm.Params(precision=prec, **kw), stream=stream)
+        lat.init(t(rr), t(rb))
+        best, _ = tune.autotune(lat, steps=3, trials=1)
+        lat.step(2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.step(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        gbs = bpl * n ** 3 / (ms / 1e3) / 1e9
+        out[name] = {"step_ms": ms, "mlups": n ** 3 / (ms / 1e3) / 1e6, "bytes_per_lu": bpl, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "tiling": list(best), "status": lbm.status_string(lat.totals()[1])}
+        lat.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def in_place_steps(rr, rb, rho, dev, stream, steps: int = 20):
     """Step times of the same two lattices with in-place (AA) streaming: one population
     buffer, a field pass plus the step kernel per step (not part of `value`)."""
@@ -480,6 +515,7 @@ def run_ours(args):
     tot_sc, rc_sc = sc.totals()
     in_place = in_place_steps(rr, rb, rho, dev, stream)
     storage16 = storage16_steps(rr, rb, rho, dev, stream)
+    emulsion = emulsion_steps(dev, stream)
     multirange = multirange_steps(dev, stream)
 
     # end to end through the public API with pinned host buffers: init from host fields,
@@ -528,6 +564,7 @@ def run_ours(args):
             "tiling": tiling,
             "in_place": in_place,
             "fp16_storage": storage16,
+            "emulsion": emulsion,
             "multirange": multirange,
             "status": {"cg": lbm.status_string(rc_cg), "sc": lbm.status_string(rc_sc),
                        "cg_mass_r": tot_cg["mass_r"], "sc_mass": tot_sc["mass_r"]},

@@ -238,6 +238,25 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* dst);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* src, const uint8_t* solid);
 
+/* Raw state of a range of z-planes, for domain decomposition (the halo planes of a z-slab
+ * sub-domain; Sec. 2.3 notes that a single layer of boundary nodes shared between processes
+ * suffices for the repulsion method).  The packed layout is that of lbm_save_state
+ * restricted to the planes [z0, z0 + nplanes): for each of the K*Q population arrays, then
+ * each of the K reference-density arrays, nplanes * nx * ny values of the storage type
+ * (reference densities FP64 for FP64 storage, FP32 otherwise), x fastest.
+ * lbm_state_planes_bytes: the packed size (0 for a NULL context or nplanes < 1).
+ * lbm_get_state_planes copies the planes of the state the next step reads into buf,
+ * lbm_set_state_planes writes buf into them; buf is host (pinned or pageable) or device
+ * memory owned by the caller; both are enqueued on the context's stream and return at once
+ * (pageable host memory makes the copy synchronous, as cudaMemcpyAsync does).  A state
+ * frozen by a tripped blow-up check is not tracked here (read lbm_moments' status).
+ * Errors: LBM_EINVAL for a NULL argument, z0 < 0, nplanes < 1 or z0 + nplanes > nz;
+ * LBM_ESTATE before lbm_init_fields or with in-place streaming (LBM_STREAM_AA);
+ * LBM_ECUDA on a CUDA error. */
+size_t lbm_state_planes_bytes(const lbm_ctx* ctx, int32_t nplanes);
+lbm_status lbm_get_state_planes(lbm_ctx* ctx, int32_t z0, int32_t nplanes, void* buf);
+lbm_status lbm_set_state_planes(lbm_ctx* ctx, int32_t z0, int32_t nplanes, const void* buf);
+
 /* Allocation-free totals (the paper has no counterpart; this serves callers that cannot
  * call cudaMalloc, e.g. a plugin whose host application's caching allocator has reserved
  * the device memory, or a loop that must never enter the driver's allocation path).

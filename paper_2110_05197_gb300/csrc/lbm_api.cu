@@ -472,6 +472,49 @@ lbm_status lbm_save_state(lbm_ctx* c, void* dst) {
   return hd.status ? LBM_EUNSTABLE : LBM_OK;
 }
 
+size_t lbm_state_planes_bytes(const lbm_ctx* c, int32_t nplanes) {
+  if (!c || nplanes < 1) return 0;
+  const size_t per = (size_t)nplanes * c->p.nx * c->p.ny;
+  return per * ((size_t)c->K * c->Q * c->elt + (size_t)c->K * c->relt);
+}
+
+namespace {
+// Copies between the current buffer pair's planes [z0, z0 + np) and a packed buffer:
+// every population array's planes, then every reference array's (to_buf: state -> buf).
+lbm_status copy_planes(lbm_ctx* c, int32_t z0, int32_t np, void* buf, bool to_buf) {
+  if (!c || !buf || z0 < 0 || np < 1 || z0 + np > c->p.nz) return LBM_EINVAL;
+  if (c->sticky != LBM_OK) return c->sticky;
+  if (!c->initialised || c->aa) return LBM_ESTATE;
+  const size_t plane = (size_t)c->p.nx * c->p.ny;
+  const size_t pb = np * plane * c->elt, rb = np * plane * c->relt;
+  unsigned char* f = static_cast<unsigned char*>(c->f[c->cur]);
+  unsigned char* r = static_cast<unsigned char*>(c->r[c->cur]);
+  unsigned char* b = static_cast<unsigned char*>(buf);
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < c->K * c->Q && e == cudaSuccess; a++) {
+    unsigned char* st = f + ((size_t)a * c->N + z0 * plane) * c->elt;
+    unsigned char* bb = b + a * pb;
+    e = to_buf ? cudaMemcpyAsync(bb, st, pb, cudaMemcpyDefault, c->stream)
+               : cudaMemcpyAsync(st, bb, pb, cudaMemcpyDefault, c->stream);
+  }
+  for (int k = 0; k < c->K && e == cudaSuccess; k++) {
+    unsigned char* st = r + ((size_t)k * c->N + z0 * plane) * c->relt;
+    unsigned char* bb = b + (size_t)c->K * c->Q * pb + k * rb;
+    e = to_buf ? cudaMemcpyAsync(bb, st, rb, cudaMemcpyDefault, c->stream)
+               : cudaMemcpyAsync(st, bb, rb, cudaMemcpyDefault, c->stream);
+  }
+  return e == cudaSuccess ? LBM_OK : fail(c, e);
+}
+}  // namespace
+
+lbm_status lbm_get_state_planes(lbm_ctx* c, int32_t z0, int32_t nplanes, void* buf) {
+  return copy_planes(c, z0, nplanes, buf, true);
+}
+
+lbm_status lbm_set_state_planes(lbm_ctx* c, int32_t z0, int32_t nplanes, const void* buf) {
+  return copy_planes(c, z0, nplanes, const_cast<void*>(buf), false);
+}
+
 lbm_status lbm_load_state(lbm_ctx* c, const void* src, const uint8_t* solid) {
   if (!c || !src) return LBM_EINVAL;
   if (c->sticky != LBM_OK) return c->sticky;

@@ -70,6 +70,9 @@ SIGNATURES = {
     "lbm_save_state": (ctypes.c_int, [_VP, _VP]),
     "lbm_load_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "lbm_totals_noalloc": (ctypes.c_int, [ctypes.POINTER(_CParams), _VP, _VP, _VP, _VP]),
+    "lbm_state_planes_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int32]),
+    "lbm_get_state_planes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP]),
+    "lbm_set_state_planes": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
                                         ctypes.POINTER(ctypes.c_size_t), _VP, ctypes.POINTER(_VP)]),
     "lbm_batch_units": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
@@ -308,6 +311,21 @@ class Lattice:
         t = np.zeros(NTOTALS)
         rc = self.moments_into(totals=t)
         return dict(zip(TOTAL_NAMES, t.tolist())), rc
+
+    def state_planes(self, z0: int, nplanes: int, out=None):
+        """Raw state of the planes [z0, z0 + nplanes) as a packed uint8 device tensor
+        (lbm_get_state_planes; enqueued on the lattice's stream)."""
+        import torch
+        nb = int(lib().lbm_state_planes_bytes(self._h, nplanes))
+        if out is None:
+            out = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        _check(lib().lbm_get_state_planes(self._h, z0, nplanes, _ptr(out)), "lbm_get_state_planes")
+        return out
+
+    def set_state_planes(self, z0: int, nplanes: int, buf):
+        """Write packed raw state (state_planes' layout) into the planes [z0, z0 + nplanes)."""
+        _check(lib().lbm_set_state_planes(self._h, z0, nplanes, _ptr(buf)), "lbm_set_state_planes")
+        return self
 
     def pops(self, device: bool = True):
         import torch
