@@ -10,9 +10,10 @@
 //   1. reads its own node of plane J from the raw plane buffer (a TMA copy of the tile's
 //      TX x (TY + 2) rows: interior rows plus one halo row above and below), forms the
 //      component densities (comp_state) and keeps in registers what the collision of that
-//      node needs one plane later: the colour sums t_i = g^R_i + g^B_i of the stored
-//      deviations (the CG collision acts on the total population and never reads a single
-//      colour's input) and the density bookkeeping (rho, dq, d per colour);
+//      node needs one plane later: the density bookkeeping (rho, dq, d per colour) and the
+//      colour sums t_i = g^R_i + g^B_i of the stored deviations (the CG collision acts on
+//      the total population and never reads a single colour's input; SC: the deviations);
+//      for CG the sums are read after step 4 instead (ring_late_hold);
 //   2. writes the node's stencil fields into field slot J; threads of the first two tile
 //      rows also reduce one node of the top or bottom halo row;
 //   3. passes a block barrier; then the threads of the tile's first and last column send
@@ -27,10 +28,11 @@
 // scope) would make every thread wait, once per plane, until its 38 global stores of the
 // previous collision had reached L2 -- measured at a third of the step's time.  The remote
 // columns are ordered by the mbarrier's transaction count instead.
-// A raw plane buffer is only read in step 1 of its own plane, so with R buffers the copy
-// of plane J+R-1 is issued at the start of iteration J, after the block barrier of
-// iteration J-1 has retired every read of the buffer it overwrites (plane J-1's), and has
-// R-1 planes of work to land; R is 2 to 4, as shared memory allows.  Field slot J (last read by the collision of plane J-3, in iteration
+// A raw plane buffer is only read in iteration J of its own plane, so with R buffers the
+// copy of plane J+R-1 is issued at the start of iteration J (after step 3 when the sums
+// are read late), once a block barrier has retired every read of the buffer it
+// overwrites (plane J-1's), and has about R-1 planes of work to land; R is 2 to 4, as
+// shared memory allows.  Field slot J (last read by the collision of plane J-3, in iteration
 // J-2) is written locally after the block barrier of iteration J-1, and remotely by a
 // neighbour only after that neighbour has received this block's columns of plane J-1,
 // which are sent after this block's barrier of iteration J-1: four field slots.  Without
@@ -60,6 +62,14 @@ struct RingTraits<kSCMP> {
 };
 
 constexpr int kRingFields = 4;    // field slots
+// Whether the sums a thread carries to the next plane are read from the raw plane buffer
+// after the collision rather than while staging: then only one plane's sums are live
+// across the collision (fewer registers), but the plane's copy can only be issued after
+// the block barrier that retires those late reads, half a plane later.  Measured at
+// 128^3: CG in 16-bit storage 166 -> 160 us (64 x 4 tiles), 189 -> 176 us (32 x 16), FP32
+// CG unchanged; SC multiphase, whose planes are quicker, 83 -> 95 us.  So CG only.
+template <int MODEL>
+__host__ __device__ constexpr bool ring_late_hold() { return MODEL == kCG; }
 constexpr int kRingHeader = 128;  // mbarriers, then 128-byte aligned plane buffers
 
 // Blocks per SM: 16 warps per SM either as one 512-thread block or as two 256-thread
@@ -262,6 +272,7 @@ __global__ void __launch_bounds__(TX * TY, ring_blocks<TX, TY>())
   constexpr int NV = RingTraits<MODEL>::NV;
   constexpr int EX = Lay::EX, NE = Lay::NE;
   constexpr int FS = kRingFields;
+  constexpr bool kRingLateHold = ring_late_hold<MODEL>();
   // bytes of the two halo columns (all TY + 2 rows, NV fields) the x-neighbours send
   constexpr uint32_t kEdgeBytes = 2u * (TY + 2) * NV * 4u;
   // A blown-up (or timed-out) state stops stepping.  Every block still runs the same
@@ -337,11 +348,13 @@ __global__ void __launch_bounds__(TX * TY, ring_blocks<TX, TY>())
   for (int J = 0; cur.valid; J++) {
     // copy of plane J+RAW-1 into the buffer plane J-1 used (its reads retired at the last
     // block barrier)
-    if (tid == 0 && alive && ahead.valid) {
-      issue(ahead, (J + kRingRaw - 1) % kRingRaw);
-      issued = J + kRingRaw;
+    if constexpr (!kRingLateHold) {
+      if (tid == 0 && alive && ahead.valid) {
+        issue(ahead, (J + kRingRaw - 1) % kRingRaw);
+        issued = J + kRingRaw;
+      }
+      ahead.next();
     }
-    ahead.next();
     const int y0 = cur.sg.col * TY;
     const int z = cur.z;
     const bool interior_next = z >= cur.sg.z0 && z < cur.sg.z1;  // plane J is collided in iteration J+1
@@ -380,8 +393,10 @@ __global__ void __launch_bounds__(TX * TY, ring_blocks<TX, TY>())
           val[1] = c1.q;
           val[2] = out[1];
           if (own) {
+            if constexpr (!kRingLateHold) {
 #pragma unroll
-            for (int i = 0; i < Q; i++) new_hold[i] = g0[i] + g1[i];
+              for (int i = 0; i < Q; i++) new_hold[i] = g0[i] + g1[i];
+            }
             new_cs[0] = c0;
             new_cs[1] = c1;
           }
@@ -395,8 +410,10 @@ __global__ void __launch_bounds__(TX * TY, ring_blocks<TX, TY>())
           val[0] = out[0];
           val[1] = c0.q;
           if (own) {
+            if constexpr (!kRingLateHold) {
 #pragma unroll
-            for (int i = 0; i < Q; i++) new_hold[i] = g0[i];
+              for (int i = 0; i < Q; i++) new_hold[i] = g0[i];
+            }
             new_cs[0] = c0;
           }
         }
@@ -408,6 +425,14 @@ __global__ void __launch_bounds__(TX * TY, ring_blocks<TX, TY>())
       if (ty < 2) stage_node(tx + 1, ty == 0 ? 0 : TY + 1, false);
     }
     __syncthreads();  // local fields of plane J complete; iteration J-1's collision retired
+    if constexpr (kRingLateHold) {
+      // the buffer of plane J-1: its last reads (the late sums) retired at this barrier
+      if (tid == 0 && alive && ahead.valid) {
+        issue(ahead, (J + kRingRaw - 1) % kRingRaw);
+        issued = J + kRingRaw;
+      }
+      ahead.next();
+    }
     if (alive) {
       if (tx == 0 || tx == TX - 1) {
         // the tile's first column is the left neighbour's right halo column, its last
@@ -487,6 +512,20 @@ __global__ void __launch_bounds__(TX * TY, ring_blocks<TX, TY>())
           T v = g[0][i];
           if (i != 0) v += p.phi[0][grp<L>(i)] * (q0 - at(i)[NE]);
           fout[i * N32 + dest(i)] = st_s<S, T>(v);
+        }
+      }
+    }
+    if constexpr (kRingLateHold) {
+      // the colour sums of this thread's node of plane J, from its raw buffer (intact until
+      // the copy issued after the next block barrier)
+      if (alive) {
+        const S* pop = reinterpret_cast<const S*>(bufs + (J % kRingRaw) * Lay::BUF_MAIN + Lay::PM::row(ty + 1)) + tx;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+          if constexpr (MODEL == kCG)
+            new_hold[i] = ld_s<S, T>(pop[i * TX]) + ld_s<S, T>(pop[(Q + i) * TX]);
+          else
+            new_hold[i] = ld_s<S, T>(pop[i * TX]);
         }
       }
     }
