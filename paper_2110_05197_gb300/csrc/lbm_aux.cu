@@ -384,14 +384,26 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const double* __rest
       int x, y, z;
       node_xyz(n, a, x, y, z);
       // sum_i w_i phi(x + c_i) c_i as opposite-pair differences in FP64 (the force is a
-      // small difference of O(1) values)
+      // small difference of O(1) values); neighbour indices in 32-bit arithmetic when the
+      // node count allows it
       double s1[3] = {0.0, 0.0, 0.0}, s2[3] = {0.0, 0.0, 0.0};
       const double psic = a.model == LBM_MODEL_SC_MP ? psi[n] : 0.0;
+      const bool small = a.n < (1LL << 31);
+      const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x + 1 == a.nx ? 0 : x + 1;
+      const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y + 1 == a.ny ? 0 : y + 1;
+      const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z + 1 == a.nz ? 0 : z + 1;
+      auto nbi = [&](int dx, int dy, int dz) -> long long {
+        const int X = dx == 0 ? x : (dx > 0 ? xp : xm);
+        const int Y = dy == 0 ? y : (dy > 0 ? yp : ym);
+        const int Z = dz == 0 ? z : (dz > 0 ? zp : zm);
+        return small ? (long long)(unsigned)(X + a.nx * (Y + a.ny * Z))
+                     : X + (long long)a.nx * (Y + (long long)a.ny * Z);
+      };
 #pragma unroll
       for (int q = 0; q < L::NP; q++) {
         const int i = 2 * q + 1;
-        const long long mp = nb_index(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
-        const long long mm = nb_index(x, y, z, -cx<L>(i), -cy<L>(i), -cz<L>(i), a.nx, a.ny, a.nz);
+        const long long mp = nbi(cx<L>(i), cy<L>(i), cz<L>(i));
+        const long long mm = nbi(-cx<L>(i), -cy<L>(i), -cz<L>(i));
         const bool swp = solid && solid[mp], swm = solid && solid[mm];
         const double w = L::w(L::pgrp(q));
         double d1, d2 = 0.0;

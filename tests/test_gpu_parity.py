@@ -3,9 +3,9 @@ inputs, plus the library's own guarantees (tiling independence, determinism, che
 round-trip, host/device inputs, blow-up detection).
 
 Tolerances:
-  FP64: every population after 100 steps, |g - o| <= 1e-12 * max(|o|, 1e-3 rho_max): a
+  FP64: every population after 100 steps, |g - o| <= 1e-12 * max(|o|, 1e-4 rho_max): a
         population far below the density scale is a difference of O(0.1) terms, so its
-        rounding error is set by those terms, not by its own size.
+        rounding error is set by those terms, not by its own size (measured <= 4.9e-13).
   FP32: densities |g - o| <= 1e-5 * max(|o|, 1e-3 rho_max) at every node; velocities
         ||u_g - u_o||_2 <= 1e-5 ||u_o||_2 over the lattice, and no node off by more than
         3e-5 max|u_o|; per-component mass drift <= 1e-6 relative.  After 100 steps, except
@@ -33,7 +33,7 @@ if not torch.cuda.is_available():  # collected on CPU hosts only to be deselecte
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 
-def _pops_rel_err(g, o, rho_max, floor=1e-3):
+def _pops_rel_err(g, o, rho_max, floor=1e-4):
     return np.max(np.abs(g - o) / np.maximum(np.abs(o), floor * rho_max))
 
 
@@ -54,7 +54,7 @@ def test_fp64_parity_100_steps(orc, lbm, name):
     g = lat.pops().cpu().numpy()
     o = s.pops()
     err = _pops_rel_err(g, o, rm)
-    print(f"{name}: FP64 max rel err after 100 steps {err:.3e} (floor 1e-4: {_pops_rel_err(g, o, rm, 1e-4):.3e}, "
+    print(f"{name}: FP64 max rel err after 100 steps {err:.3e} (floor 1e-3: {_pops_rel_err(g, o, rm, 1e-3):.3e}, "
           f"max abs {np.max(np.abs(g - o)):.2e})")
     assert err < 1e-12
     # moments and totals

@@ -223,18 +223,22 @@ def _laplace_2d(orc, R, n=64, steps=1500, A=1e-2):
 
 
 def test_laplace_2d(orc):
-    """2D Young-Laplace: Delta P * R is the surface tension, constant across radii and
-    close to sigma_th = (4/9) A / omega_eff = 4.44e-3 (A = 1e-2, omega = 1)."""
+    """2D Young-Laplace over R = 10 ... 30: Delta P * R is the surface tension, constant
+    across radii within 5%, and at R = 20 within 5% of sigma_th = (4/9) A / omega_eff =
+    4.44e-3 (A = 1e-2, omega = 1; the paper's own error at R = 20 is a few per cent, Fig.
+    vardens).  Larger drops relax over about R^2 / nu steps, so R = 20 and 30 run 8000 and
+    9000 steps (96^2 box).  Measured errors: +2.8%, +0.4%, -0.4% at R = 10, 14, 18 and
+    +0.9%, -0.3% at R = 20, 30."""
     sig_th = 4 / 9 * 1e-2
-    vals = []
-    for R in (10, 14, 18):
-        sig, t = _laplace_2d(orc, R)
-        vals.append(sig)
-        print("Laplace 2D R=%d sigma_cal=%.5e" % (R, sig))
+    vals = {}
+    for R, n, steps in ((10, 64, 1500), (14, 64, 1500), (18, 64, 1500), (20, 96, 8000), (30, 96, 9000)):
+        sig, t = _laplace_2d(orc, R, n=n, steps=steps)
+        vals[R] = sig
+        print("Laplace 2D R=%d (%d^2, %d steps) sigma_cal=%.5e, error %+.4f" % (R, n, steps, sig, sig / sig_th - 1))
         assert t[6] < 1e-3  # spurious currents stay small
-    vals = np.array(vals)
-    assert np.ptp(vals) / vals.mean() < 0.05
-    assert abs(vals[-1] - sig_th) / sig_th < 0.08
+    v = np.array(list(vals.values()))
+    assert np.ptp(v) / v.mean() < 0.05
+    assert abs(vals[20] - sig_th) / sig_th < 0.05
 
 
 # ---------------------------------------------------------------- Shan-Chen coexistence
@@ -364,7 +368,7 @@ def test_droplet_oscillation_miller_scriven(orc):
     formula takes the run's own R_D and its measured surface tension sigma = dP R_D / 2
     (dP from the CG pressure p = sum_k rho_k (1 - alpha_k)/2 inside and outside, Eq.
     CGpressure), rho_in = rho_out = 1 and nu = (tau - 1/2)/3.  The paper reports 11.5% at
-    R_D = 11.65 (Table dropOsc); at R_D ~ 7.6 the bound is 15%, and the oscillation must
+    R_D = 11.65 (Table dropOsc); at R_D ~ 7.6 this run measures 9.5%, held to 10%, and the oscillation must
     decay.  A wrong inertia, viscosity or pressure law moves the frequency by far more."""
     from scipy.optimize import curve_fit
     n, tau, A, a = 28, 0.52, 0.02, 8.8
@@ -411,7 +415,7 @@ def test_droplet_oscillation_miller_scriven(orc):
     err = (p[3] - w2) / w2
     print(f"Miller-Scriven: R_D {RD:.3f}, sigma {sigma:.5f} (theory {4 / 9 * A * tau:.5f}), "
           f"omega_2 fit {p[3]:.5f} vs formula {w2:.5f} ({err:+.3f}), damping {p[2]:.2e}")
-    assert abs(err) < 0.15
+    assert abs(err) < 0.10   # measured -0.095 (deterministic: FP64, per-node work only)
     assert p[2] > 0
     assert 0.8 < sigma / (4 / 9 * A * tau) < 1.1   # sigma = (4/9) A / omega_eff within the Laplace error
 
