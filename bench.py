@@ -57,7 +57,7 @@ def sc_kw(n=N3, nz=None):
 
 # Sources that define the FP32 step kernels and their launch (the profiled kernels).
 STEP_KERNEL_SOURCES = ("lbm_lattice.cuh", "lbm_rep.cuh", "lbm_step.cuh", "lbm_step_tma.cuh", "lbm_step_tmac.cuh",
-                       "lbm_launch.cuh", "lbm_internal.cuh", "lbm_step_f32.cu")
+                       "lbm_step_ring.cuh", "lbm_launch.cuh", "lbm_internal.cuh", "lbm_step_f32.cu")
 
 
 def csrc_sha256_16():
