@@ -113,9 +113,23 @@ struct ExactSum<float> {
   __device__ double value() const { return double(s) + double(c); }
 };
 
+// x, y, z of node n (32-bit arithmetic whenever the node count allows it)
+__device__ __forceinline__ void node_xyz(long long n, const AuxParams& a, int& x, int& y, int& z) {
+  if (a.n < (1LL << 31)) {
+    const unsigned m = (unsigned)n, row = m / (unsigned)a.nx;
+    x = (int)(m - row * (unsigned)a.nx);
+    z = (int)(row / (unsigned)a.ny);
+    y = (int)(row - (unsigned)z * (unsigned)a.ny);
+  } else {
+    x = (int)(n % a.nx);
+    y = (int)((n / a.nx) % a.ny);
+    z = (int)(n / ((long long)a.nx * a.ny));
+  }
+}
+
 // 3 sum_i w_i phi(x + c_i) c_i with a wall neighbour replaced by the centre value.
-template <class L, class C>
-__device__ void grad_c(const double* phi, const uint8_t* solid, long long n, int x, int y, int z,
+template <class L, class C, class E>
+__device__ void grad_c(const E* phi, const uint8_t* solid, long long n, int x, int y, int z,
                        const AuxParams& a, C g[3]) {
   g[0] = g[1] = g[2] = C(0);
   for (int q = 0; q < L::NP; q++) {
@@ -148,10 +162,21 @@ __device__ void feq_dev(C rho_k, const double* phi, C nubar_en, const C u[3], co
   }
 }
 
+// Both component densities rounded to the compute type: out[k][n] = C(rho_k[n]).
+template <class C>
+__global__ void to_compute_kernel(const double* __restrict__ rr, const double* __restrict__ rb, C* __restrict__ out,
+                                  long long n) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+    out[m] = C(rr[m]);
+    out[n + m] = C(rb[m]);
+  }
+}
+
 template <class L, class S, class RT>
 __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __restrict__ ra, RT* __restrict__ rb_,
                                const double* __restrict__ rr, const double* __restrict__ rb,
-                               const double* __restrict__ U, const uint8_t* __restrict__ solid, AuxParams a) {
+                               const double* __restrict__ U, const uint8_t* __restrict__ solid,
+                               const step_t<S>* __restrict__ fc, AuxParams a) {
   using C = step_t<S>;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
     C out[L::Q];
@@ -166,7 +191,8 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
       }
       continue;
     }
-    const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+    int x, y, z;
+    node_xyz(n, a, x, y, z);
     C u[3] = {C(0), C(0), C(0)};
     if (U) {
       u[0] = C(U[n]);
@@ -175,7 +201,7 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
     }
     C en = C(0);
     if (a.model == LBM_MODEL_CG && a.enhanced) {
-      const C r = C(rr[n]), b = C(rb[n]), rho = r + b;
+      const C r = fc ? fc[n] : C(rr[n]), b = fc ? fc[a.n + n] : C(rb[n]), rho = r + b;
       en = C(1) / ((r / rho) / C(a.nu_r) + (b / rho) / C(a.nu_b));  // Eq. interpVisc
     }
     // Only pair 0 is written for fluid nodes: the first step writes every population and
@@ -184,7 +210,12 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
       const double* phi = k == 0 ? rr : rb;
       const RT rref = RT(phi[n]);  // reference density: the initial density, rounded
       C g[3] = {C(0), C(0), C(0)};
-      if (a.model == LBM_MODEL_CG) grad_c<L, C>(phi, solid, n, x, y, z, a, g);
+      if (a.model == LBM_MODEL_CG) {
+        if (fc)
+          grad_c<L, C>(fc + (long long)k * a.n, solid, n, x, y, z, a, g);
+        else
+          grad_c<L, C>(phi, solid, n, x, y, z, a, g);
+      }
       feq_dev<L, C>(C(phi[n]), a.phi[k], en, u, g, C(phi[n] - (double)rref), out);
       ra[(long long)k * a.n + n] = rref;
       for (int i = 0; i < L::Q; i++) {
@@ -247,19 +278,6 @@ __global__ void aa_gather_kernel(const S* __restrict__ f, S* __restrict__ out, c
   }
 }
 
-// x, y, z of node n (32-bit arithmetic whenever the node count allows it)
-__device__ __forceinline__ void node_xyz(long long n, const AuxParams& a, int& x, int& y, int& z) {
-  if (a.n < (1LL << 31)) {
-    const unsigned m = (unsigned)n, row = m / (unsigned)a.nx;
-    x = (int)(m - row * (unsigned)a.nx);
-    z = (int)(row / (unsigned)a.ny);
-    y = (int)(row - (unsigned)z * (unsigned)a.ny);
-  } else {
-    x = (int)(n % a.nx);
-    y = (int)((n / a.nx) % a.ny);
-    z = (int)(n / ((long long)a.nx * a.ny));
-  }
-}
 
 // One pass over the populations: the component densities rr, rb (FP64, as exact as FP64
 // summation), psi of Eq. pseudopotential (SC multiphase, FP64), the momentum
@@ -313,6 +331,10 @@ __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__
   }
 }
 
+// x is finite: its exponent field is not all ones (integer test of the high word; GB300
+// runs FP64 compares at its low FP64 rate).
+__device__ __forceinline__ bool finite_bits(double x) { return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000; }
+
 // ---- fixed-order block reductions ----
 struct Acc {
   double v[LBM_NTOTALS];
@@ -350,6 +372,29 @@ __device__ void block_reduce(Acc& a) {
   }
 }
 
+// Fixed-order reduction of the nblk block partials into the totals and the blow-up status
+// (all threads of one block take part).
+__device__ void reduce_partials(const double* partials, int nblk, lbm_diag* d, int cur, const AuxParams& a) {
+  Acc acc;
+  acc_init(acc);
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    Acc o;
+    for (int s = 0; s < LBM_NTOTALS; s++) o.v[s] = __ldcg(&partials[b * LBM_NTOTALS + s]);
+    acc_merge(acc, o);
+  }
+  block_reduce(acc);
+  if (threadIdx.x == 0) {
+    acc.v[6] = sqrt(acc.v[6]);  // max |u| from max |u|^2 (sqrt is monotonic and correctly rounded)
+    int st = 0;
+    if (acc.v[7] > 0 || !isfinite(acc.v[0]) || !isfinite(acc.v[1])) st |= 1;
+    if (acc.v[8] < -a.neg_tol || acc.v[9] < -a.neg_tol) st |= 2;
+    if (!(acc.v[6] <= a.umax)) st |= 4;
+    for (int s = 0; s < LBM_NTOTALS; s++) d->totals[s] = acc.v[s];
+    if (d->status == 0 && st != 0) d->trip_buf = cur;
+    d->status |= st;
+  }
+}
+
 // Per-node velocity and the block partials of the totals, from the staged densities and
 // momentum (densities_kernel): no population is read again.  u (force-shifted, Eq.
 // guoforce) may be written over jm (uo == jm): each node reads its own momentum first.
@@ -363,7 +408,8 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const double* __rest
                                                             const uint8_t* __restrict__ solid, double* uo,
                                                             double* __restrict__ partials, AuxParams a,
                                                             const step_t<S>* __restrict__ colour,
-                                                            const step_t<S>* __restrict__ normals, RepParams rp) {
+                                                            const step_t<S>* __restrict__ normals, RepParams rp,
+                                                            lbm_diag* __restrict__ d, int cur) {
   using C = step_t<S>;  // per-node arithmetic of the multirange belts; the sums below are FP64
   Acc acc;
   acc_init(acc);
@@ -371,7 +417,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const double* __rest
     const bool wall = solid && solid[n];
     const double j[3] = {jm[n], jm[a.n + n], jm[2 * a.n + n]};
     const double r = rr[n], b = rb[n], rho = r + b;
-    const int bad = !(isfinite(r) && isfinite(b) && isfinite(j[0]) && isfinite(j[1]) && isfinite(j[2]));
+    const int bad = !(finite_bits(r) && finite_bits(b) && finite_bits(j[0]) && finite_bits(j[1]) && finite_bits(j[2]));
     double F[3] = {a.body[0], a.body[1], a.body[2]};
     if (!wall && a.model == LBM_MODEL_CG && normals) {
       int x, y, z;
@@ -491,31 +537,22 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const double* __rest
     acc.v[9] = fmin(acc.v[9], b);
   }
   block_reduce(acc);
-  if (threadIdx.x == 0)
+  // The block that finishes last reduces every block's partial (in block order, whatever
+  // the finishing order): partial written, fence, count; the counter goes back to 0.
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
     for (int s = 0; s < LBM_NTOTALS; s++) partials[blockIdx.x * LBM_NTOTALS + s] = acc.v[s];
+    __threadfence();
+    last = atomicAdd(&d->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    reduce_partials(partials, gridDim.x, d, cur, a);
+    if (threadIdx.x == 0) d->done = 0;
+  }
 }
 
-__global__ void __launch_bounds__(kDiagThreads) finalize_kernel(const double* __restrict__ partials, int nblk,
-                                                                lbm_diag* __restrict__ d, int cur, AuxParams a) {
-  Acc acc;
-  acc_init(acc);
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    Acc o;
-    for (int s = 0; s < LBM_NTOTALS; s++) o.v[s] = partials[b * LBM_NTOTALS + s];
-    acc_merge(acc, o);
-  }
-  block_reduce(acc);
-  if (threadIdx.x == 0) {
-    acc.v[6] = sqrt(acc.v[6]);  // max |u| from max |u|^2 (sqrt is monotonic and correctly rounded)
-    int st = 0;
-    if (acc.v[7] > 0 || !isfinite(acc.v[0]) || !isfinite(acc.v[1])) st |= 1;
-    if (acc.v[8] < -a.neg_tol || acc.v[9] < -a.neg_tol) st |= 2;
-    if (!(acc.v[6] <= a.umax)) st |= 4;
-    for (int s = 0; s < LBM_NTOTALS; s++) d->totals[s] = acc.v[s];
-    if (d->status == 0 && st != 0) d->trip_buf = cur;
-    d->status |= st;
-  }
-}
 
 int grid_for(long long n, int threads, int cap) {
   long long b = (n + threads - 1) / threads;
@@ -526,11 +563,24 @@ int grid_for(long long n, int threads, int cap) {
 
 template <class L, class S, class RT>
 cudaError_t init_t(lbm_ctx* c, const double* rr, const double* rb, const double* u) {
+  using C = step_t<S>;
   const AuxParams a = aux_params(c);
+  // CG in a compute type narrower than FP64: the gradient stencil reads each density 19
+  // times, so the fields are rounded to the compute type once, into the free tail of the
+  // staging buffer ([5N, 6N) doubles hold 2N values of at most 4 bytes); the stencil gives
+  // the same values as rounding at every read
+  C* fc = nullptr;
+  if (sizeof(C) < sizeof(double) && c->p.model == LBM_MODEL_CG) {
+    fc = reinterpret_cast<C*>(c->stage + 5 * c->N);
+    to_compute_kernel<C><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(rr, rb, fc, c->N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+  }
   // in-place streaming: one buffer pair (the second pointers alias the first)
   init_eq_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
       static_cast<S*>(c->f[0]), c->aa ? nullptr : static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]),
-      c->aa ? nullptr : static_cast<RT*>(c->r[1]), rr, rb, u, c->has_walls ? c->solid : nullptr, a);
+      c->aa ? nullptr : static_cast<RT*>(c->r[1]), rr, rb, u, c->has_walls ? c->solid : nullptr, fc, a);
   return cudaGetLastError();
 }
 
@@ -585,11 +635,9 @@ cudaError_t diag_t(lbm_ctx* c, double* uo) {
   }
   diag_kernel<L, S, RT><<<c->nblk_diag, kDiagThreads, 0, c->stream>>>(
       rr, rb, psi, jm, mrpsi, c->has_walls ? c->solid : nullptr, uo, c->partials, a,
-      static_cast<const step_t<S>*>(c->colour), static_cast<const step_t<S>*>(c->normals), rep_params(c));
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  finalize_kernel<<<1, kDiagThreads, 0, c->stream>>>(c->partials, c->nblk_diag, c->diag, c->cur, a);
-  c->launches += 3;
+      static_cast<const step_t<S>*>(c->colour), static_cast<const step_t<S>*>(c->normals), rep_params(c), c->diag,
+      c->cur);
+  c->launches += 2;
   return cudaGetLastError();
 }
 

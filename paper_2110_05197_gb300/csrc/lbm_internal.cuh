@@ -16,7 +16,9 @@ struct lbm_diag {
   int status;       // 0 ok; bit 0 non-finite, bit 1 negative density, bit 2 |u| too large
   int trip_buf;     // population buffer (0/1) holding the state the check tripped on; after a
                     // trip the step kernels write nothing, so that buffer stays the state
-  int pad[2];
+  unsigned done;    // blocks of the running diagnostics pass that have written their partials
+                    // (the last one reduces them and puts it back to 0)
+  int pad;
 };
 
 struct lbm_ctx {
