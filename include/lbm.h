@@ -195,7 +195,8 @@ lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t tx, int32_t ty, int32_t tz);
  * is bitwise the same alone or in any mix (it may differ by a few ulps from a lattice
  * stepped with lbm_step_* on the TMA-staged kernel).  Jobs must be initialised, periodic
  * (no walls), without the repulsion force, with two-buffer streaming (LBM_STREAM_AB), of
- * the batch's storage precision and on the batch's stream.  The periodic diagnostics (diag_every) do not run inside a batch; call
+ * the batch's storage precision and on the batch's stream, with K * Q * N < 2^31 (the
+ * batched kernel indexes in 32 bits).  The periodic diagnostics (diag_every) do not run inside a batch; call
  * lbm_moments per job.
  *
  * lbm_batch_create: precision LBM_FP32, LBM_FP16 or LBM_BF16; capacity max_jobs lattices

@@ -113,18 +113,9 @@ struct ExactSum<float> {
   __device__ double value() const { return double(s) + double(c); }
 };
 
-// x, y, z of node n (32-bit arithmetic whenever the node count allows it)
+// x, y, z of node n
 __device__ __forceinline__ void node_xyz(long long n, const AuxParams& a, int& x, int& y, int& z) {
-  if (a.n < (1LL << 31)) {
-    const unsigned m = (unsigned)n, row = m / (unsigned)a.nx;
-    x = (int)(m - row * (unsigned)a.nx);
-    z = (int)(row / (unsigned)a.ny);
-    y = (int)(row - (unsigned)z * (unsigned)a.ny);
-  } else {
-    x = (int)(n % a.nx);
-    y = (int)((n / a.nx) % a.ny);
-    z = (int)(n / ((long long)a.nx * a.ny));
-  }
+  node_coords(n, a.nx, a.ny, a.n, x, y, z);
 }
 
 // 3 sum_i w_i phi(x + c_i) c_i with a wall neighbour replaced by the centre value.

@@ -141,6 +141,8 @@ lbm_status lbm_batch_set(lbm_batch* b, lbm_ctx* const* ctxs, const int32_t* nste
     if (c->p.precision != b->precision || c->has_walls || c->rep || c->aa || c->p.model == LBM_MODEL_SC_MR ||
         c->stream != b->stream)
       return LBM_EINVAL;
+    // the batched kernel indexes in 32 bits
+    if ((long long)c->K * c->Q * c->N >= (1LL << 31)) return LBM_EINVAL;
     nunits += units_of(c);
   }
   if (nunits > b->max_units) return LBM_EINVAL;

@@ -62,18 +62,18 @@ __device__ __forceinline__ void batch_march(const BatchJob<T, S, RT>& job, const
   const RepParams rp{};
   if (job.lattice == LBM_D3Q19) {
     if (job.model == LBM_MODEL_CG)
-      march_segment<D3Q19, T, S, RT, kCG, false, false>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D3Q19, T, S, RT, kCG, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else if (job.model == LBM_MODEL_SC_MP)
-      march_segment<D3Q19, T, S, RT, kSCMP, false, false>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D3Q19, T, S, RT, kSCMP, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else
-      march_segment<D3Q19, T, S, RT, kSC2C, false, false>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D3Q19, T, S, RT, kSC2C, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
   } else {
     if (job.model == LBM_MODEL_CG)
-      march_segment<D2Q9, T, S, RT, kCG, false, false>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D2Q9, T, S, RT, kCG, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else if (job.model == LBM_MODEL_SC_MP)
-      march_segment<D2Q9, T, S, RT, kSCMP, false, false>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D2Q9, T, S, RT, kSCMP, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else
-      march_segment<D2Q9, T, S, RT, kSC2C, false, false>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D2Q9, T, S, RT, kSC2C, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
   }
 }
 

@@ -67,4 +67,19 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 template <class L>
 __host__ __device__ constexpr int grp(int i) { return i == 0 ? 0 : L::pgrp((i - 1) >> 1); }
 
+// Coordinates (x, y, z) of node n = x + nx (y + ny z) of a lattice of N nodes, in 32-bit
+// arithmetic whenever N allows it (64-bit integer division is a long instruction sequence).
+__device__ __forceinline__ void node_coords(long long n, int nx, int ny, long long N, int& x, int& y, int& z) {
+  if (N < (1LL << 31)) {
+    const unsigned m = (unsigned)n, row = m / (unsigned)nx;
+    x = (int)(m - row * (unsigned)nx);
+    z = (int)(row / (unsigned)ny);
+    y = (int)(row - (unsigned)z * (unsigned)ny);
+  } else {
+    x = (int)(n % nx);
+    y = (int)((n / nx) % ny);
+    z = (int)(n / ((long long)nx * ny));
+  }
+}
+
 }  // namespace lbm

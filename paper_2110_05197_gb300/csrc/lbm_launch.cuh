@@ -227,8 +227,8 @@ bool ring_eligible(const lbm_ctx* c) {
 
 // Field-pass step (in-place streaming, or the multirange model): the field pass, then the
 // step kernel, both over all nodes.
-template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
-cudaError_t launch_fp_t(lbm_ctx* c) {
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, class I>
+cudaError_t launch_fp_i(lbm_ctx* c) {
   if constexpr (REP) {
     cudaError_t e = launch_rep_prepass_t<L, T, S, RT>(c, c->cur);
     if (e != cudaSuccess) return e;
@@ -254,7 +254,7 @@ cudaError_t launch_fp_t(lbm_ctx* c) {
     // faster (in-place SC-MP 128^3: 142 vs 162 us), so they keep fp_step_kernel
     constexpr int H = 2;
     constexpr size_t smem = fpt_smem_bytes<T, MODEL, WALLS, H>();
-    auto kern = fpt_step_kernel<L, T, S, RT, MODEL, WALLS, REP, H>;
+    auto kern = fpt_step_kernel<L, T, S, RT, MODEL, WALLS, REP, H, I>;
     static int occ = 0;  // resident blocks per SM of this instantiation
     if (occ == 0) {
       if (smem > 48 * 1024) {
@@ -273,10 +273,58 @@ cudaError_t launch_fp_t(lbm_ctx* c) {
                                                       static_cast<const T*>(c->colour),
                                                       static_cast<const T*>(c->normals), rep_params(c), mode);
   } else {
-    fp_step_kernel<L, T, S, RT, MODEL, WALLS, REP><<<grid, 256, 0, c->stream>>>(
+    fp_step_kernel<L, T, S, RT, MODEL, WALLS, REP, I><<<grid, 256, 0, c->stream>>>(
         fin, fout, rin, rout, fld, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour),
         static_cast<const T*>(c->normals), rep_params(c), mode);
   }
+  return cudaGetLastError();
+}
+
+// Field-pass step with 32-bit indices where every index fits (FP64 storage: 64-bit).
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
+cudaError_t launch_fp_t(lbm_ctx* c) {
+  if constexpr (sizeof(T) < 8) {
+    if ((long long)c->K * c->Q * c->N < (1LL << 31)) return launch_fp_i<L, T, S, RT, MODEL, WALLS, REP, int>(c);
+  }
+  return launch_fp_i<L, T, S, RT, MODEL, WALLS, REP, long long>(c);
+}
+
+// Generic plane-marching step (step_kernel) with index type I.
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, class I>
+cudaError_t launch_generic_t(lbm_ctx* c) {
+  const int tx = c->tx, ty = c->ty;
+  const size_t smem = step_smem_bytes<L, T, MODEL, WALLS>(tx, ty);
+  static size_t smem_set = 0;  // largest dynamic shared memory opted in so far
+  if (smem > 48 * 1024 && smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<L, T, S, RT, MODEL, WALLS, REP, I>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
+  dim3 block(tx, ty, 1);
+  StepParams<T> sp = make_step_params<T>(c);
+  if (c->tz == 0) {
+    const void* fn = reinterpret_cast<const void*>(step_kernel<L, T, S, RT, MODEL, WALLS, REP, I>);
+    if (c->occ_fn != fn || c->occ_tx != tx || c->occ_ty != ty) {
+      int nb = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<L, T, S, RT, MODEL, WALLS, REP, I>,
+                                                                    tx * ty, smem);
+      if (e != cudaSuccess) return e;
+      c->occ_fn = fn;
+      c->occ_tx = tx;
+      c->occ_ty = ty;
+      c->occ_blocks = nb > 0 ? nb : 1;
+    }
+    persistent_plan(sp, c->nsm * c->occ_blocks);
+  }
+  dim3 grid(sp.nblk, 1, 1);
+  const S* fin = static_cast<const S*>(c->f[c->cur]);
+  S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
+  const RT* rin = static_cast<const RT*>(c->r[c->cur]);
+  RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
+  step_kernel<L, T, S, RT, MODEL, WALLS, REP, I><<<grid, block, smem, c->stream>>>(
+      fin, fout, rin, rout, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour),
+      static_cast<const T*>(c->normals), rep_params(c));
   return cudaGetLastError();
 }
 
@@ -330,40 +378,12 @@ cudaError_t launch_step_t(lbm_ctx* c) {
     cudaError_t e = launch_rep_prepass_t<L, T, S, RT>(c, c->cur);
     if (e != cudaSuccess) return e;
   }
-  const int tx = c->tx, ty = c->ty;
-  const size_t smem = step_smem_bytes<L, T, MODEL, WALLS>(tx, ty);
-  static size_t smem_set = 0;  // largest dynamic shared memory opted in so far
-  if (smem > 48 * 1024 && smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<L, T, S, RT, MODEL, WALLS, REP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    smem_set = smem;
+  // 32-bit node and array indices where every index fits (FP64 storage keeps 64-bit ones:
+  // its step is bound by the FP64 rate, not by index arithmetic)
+  if constexpr (sizeof(T) < 8) {
+    if ((long long)c->K * c->Q * c->N < (1LL << 31)) return launch_generic_t<L, T, S, RT, MODEL, WALLS, REP, int>(c);
   }
-  dim3 block(tx, ty, 1);
-  StepParams<T> sp = make_step_params<T>(c);
-  if (c->tz == 0) {
-    const void* fn = reinterpret_cast<const void*>(step_kernel<L, T, S, RT, MODEL, WALLS, REP>);
-    if (c->occ_fn != fn || c->occ_tx != tx || c->occ_ty != ty) {
-      int nb = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<L, T, S, RT, MODEL, WALLS, REP>,
-                                                                    tx * ty, smem);
-      if (e != cudaSuccess) return e;
-      c->occ_fn = fn;
-      c->occ_tx = tx;
-      c->occ_ty = ty;
-      c->occ_blocks = nb > 0 ? nb : 1;
-    }
-    persistent_plan(sp, c->nsm * c->occ_blocks);
-  }
-  dim3 grid(sp.nblk, 1, 1);
-  const S* fin = static_cast<const S*>(c->f[c->cur]);
-  S* fout = static_cast<S*>(c->f[c->cur ^ 1]);
-  const RT* rin = static_cast<const RT*>(c->r[c->cur]);
-  RT* rout = static_cast<RT*>(c->r[c->cur ^ 1]);
-  step_kernel<L, T, S, RT, MODEL, WALLS, REP><<<grid, block, smem, c->stream>>>(
-      fin, fout, rin, rout, c->solid, &c->diag->status, sp, static_cast<const T*>(c->colour),
-      static_cast<const T*>(c->normals), rep_params(c));
-  return cudaGetLastError();
+  return launch_generic_t<L, T, S, RT, MODEL, WALLS, REP, long long>(c);
   }
 }
 

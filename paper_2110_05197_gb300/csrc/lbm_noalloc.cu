@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kThreads) part_kernel(const double* __restrict
     if (a.model != LBM_MODEL_CG) {
       // SC force: Eq. interactionforceMP (psi of Eq. pseudopotential) or the cross force of
       // Eq. doublebeltrepulsionforce2; a wall neighbour takes the centre value
-      const int x = (int)(n % a.nx), y = (int)((n / a.nx) % a.ny), z = (int)(n / ((long long)a.nx * a.ny));
+      int x, y, z;
+      node_coords(n, a.nx, a.ny, a.n, x, y, z);
       const double psic = a.rho0 * (1.0 - exp(-r / a.rho0));
       double s1[3] = {0.0, 0.0, 0.0}, s2[3] = {0.0, 0.0, 0.0};
       for (int i = 1; i < L::Q; i++) {

@@ -45,7 +45,8 @@ template <class L, class T>
 __global__ void normals_kernel(const T* __restrict__ colour, const uint8_t* __restrict__ solid,
                                T* __restrict__ normals, RepParams a) {
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(m % a.nx), y = (int)((m / a.nx) % a.ny), z = (int)(m / ((long long)a.nx * a.ny));
+    int x, y, z;
+    node_coords(m, a.nx, a.ny, a.n, x, y, z);
     T g[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int q = 0; q < L::NP; q++) {

@@ -560,8 +560,9 @@ struct StepArrays {
 // step with the block's TX x TY threads; smem_raw holds step_smem_bytes() bytes.  Ends with
 // a block barrier, so the caller may reuse shared memory right away.
 // REP (CG only): add the repulsion force of Eq. repForce from the pre-pass fields
-// colour / normals (lbm_rep.cuh).
-template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
+// colour / normals (lbm_rep.cuh).  I: the integer type of node and array indices, int
+// when K * Q * N < 2^31 (the launcher's choice), else long long.
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, class I = long long>
 __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const StepParams<T>& p,
                                               const T* __restrict__ colour, const T* __restrict__ normals,
                                               const RepParams& rp, const Segment& sg,
@@ -580,7 +581,7 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
   const int EX = TX + 2;
   const int NE = EX * (TY + 2), NI = TX * TY;
   const int tid = threadIdx.y * TX + threadIdx.x;
-  const long long N = p.n;
+  const I N = I(p.n);
   const int x0 = (sg.col % p.ncx) * TX, y0 = (sg.col / p.ncx) * TY;
 
   T* fld = reinterpret_cast<T*>(smem_raw);           // [NPL][NV][NE]
@@ -595,7 +596,7 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
     for (int e = tid; e < NE; e += NI) {
       const int ey = e / EX, ex = e - ey * EX;
       const int gx = wrap(x0 - 1 + ex, p.nx), gy = wrap(y0 - 1 + ey, p.ny);
-      const long long n = gx + (long long)p.nx * (gy + (long long)p.ny * gz);
+      const I n = gx + I(p.nx) * (gy + I(p.ny) * gz);
       const bool inner = pb >= 0 && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY;
       const int ii = (ey - 1) * TX + (ex - 1);
       T rho[2] = {T(0), T(0)};
@@ -603,8 +604,8 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
       for (int k = 0; k < K; k++) {
         T v[Q];
 #pragma unroll
-        for (int i = 0; i < Q; i++) v[i] = ld_s<S, T>(fin[(long long)(k * Q + i) * N + n]);
-        const T r_old = T(rin[(long long)k * N + n]);
+        for (int i = 0; i < Q; i++) v[i] = ld_s<S, T>(fin[I(k * Q + i) * N + n]);
+        const T r_old = T(rin[I(k) * N + n]);
         const CompState<T> c = comp_state<L, T, RT>(v, r_old);
         rho[k] = c.rho;
         fld[(sl * NV + NF + k) * NE + e] = c.q;
@@ -658,9 +659,9 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
     }
     // new reference densities of this node
     const int zz = z, zm = zz == 0 ? p.nz - 1 : zz - 1, zpp = zz + 1 >= p.nz ? 0 : zz + 1;
-    const long long n0 = gx + (long long)p.nx * (gy + (long long)p.ny * zz);
+    const I n0 = gx + I(p.nx) * (gy + I(p.ny) * zz);
 #pragma unroll
-    for (int k = 0; k < K; k++) rout[(long long)k * N + n0] = RT(cs[k].q);
+    for (int k = 0; k < K; k++) rout[I(k) * N + n0] = RT(cs[k].q);
     // push to y = x + c_i (periodic), re-referenced to phi_i q(y); halfway bounce-back to
     // x, direction opp(i), at walls
 #pragma unroll
@@ -669,7 +670,7 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
       const int X = dxv == 0 ? gx : (dxv > 0 ? xp : xm);
       const int Y = dyv == 0 ? gy : (dyv > 0 ? yp : ym);
       const int Z = dzv == 0 ? zz : (dzv > 0 ? zpp : zm);
-      long long nd = X + (long long)p.nx * (Y + (long long)p.ny * Z);
+      I nd = X + I(p.nx) * (Y + I(p.ny) * Z);
       int id = i;
       const int sl = slot_of(dzv);
       const int ed = e0 + dyv * EX + dxv;
@@ -685,7 +686,7 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
       for (int k = 0; k < K; k++) {
         T v = g[k][i];
         if (i != 0 && !bounce) v += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(sl * NV + NF + k) * NE + ed]);
-        fout[(long long)(k * Q + id) * N + nd] = st_s<S, T>(v);
+        fout[I(k * Q + id) * N + nd] = st_s<S, T>(v);
       }
     }
   };
@@ -712,7 +713,7 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
   }
 }
 
-template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, class I = long long>
 __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
     const S* __restrict__ fin, S* __restrict__ fout, const RT* __restrict__ rin, RT* __restrict__ rout,
     const uint8_t* __restrict__ solid, const int* __restrict__ status, const __grid_constant__ StepParams<T> p,
@@ -722,7 +723,7 @@ __global__ void __launch_bounds__(256, min_blocks<T>()) step_kernel(
   const StepArrays<S, RT> a{fin, fout, rin, rout, solid};
   WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
   Segment sg;
-  while (work.pop(sg)) march_segment<L, T, S, RT, MODEL, WALLS, REP>(a, p, colour, normals, rp, sg, smem_raw);
+  while (work.pop(sg)) march_segment<L, T, S, RT, MODEL, WALLS, REP, I>(a, p, colour, normals, rp, sg, smem_raw);
 }
 
 }  // namespace lbm

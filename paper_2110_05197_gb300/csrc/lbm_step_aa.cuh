@@ -44,7 +44,8 @@ template <class L>
 __device__ __forceinline__ long long aa_index_n(int k, int i, long long n, int nx, int ny, int nz, long long N,
                                                 bool odd) {
   if (!odd || i == 0) return (long long)(k * L::Q + i) * N + n;
-  const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+  int x, y, z;
+  node_coords(n, nx, ny, N, x, y, z);
   return aa_index<L>(k, i, n, x, y, z, nx, ny, nz, N, odd);
 }
 
@@ -60,7 +61,8 @@ __global__ void __launch_bounds__(256) fp_fields_kernel(const S* __restrict__ f,
   const long long N = p.n;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
     if (solid && solid[n]) continue;  // wall values are never read: the stencil substitutes the centre
-    const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+    int x, y, z;
+    node_coords(n, p.nx, p.ny, N, x, y, z);
     T rho[2] = {T(0), T(0)};
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(256) fp_fields_kernel(const S* __restrict__ f,
 // per-node code as the plane-marching kernels), streaming.  mode 0: two buffers (read fin,
 // rin; push into fout, rout); mode 1 / 2: in place at even / odd layout parity (fin == fout,
 // rin == rout; the pointers may alias, so none is restrict-qualified).
-template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP>
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, class I = long long>
 __global__ void __launch_bounds__(256, min_blocks<T>())
     fp_step_kernel(const S* fin, S* fout, const RT* rin, RT* rout, const T* __restrict__ fld,
                    const uint8_t* __restrict__ solid, const int* __restrict__ status,
@@ -91,18 +93,19 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
   if (*status != 0) return;
   const bool inplace = mode != 0, odd = mode == 2;
   constexpr int Q = L::Q, K = ModelTraits<MODEL>::K, NF = ModelTraits<MODEL>::NF;
-  const long long N = p.n;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+  const I N = I(p.n);
+  for (I n = blockIdx.x * I(blockDim.x) + threadIdx.x; n < N; n += I(gridDim.x) * blockDim.x) {
     if (WALLS && solid[n]) continue;
-    const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+    int x, y, z;
+    node_coords(n, p.nx, p.ny, N, x, y, z);
     const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x + 1 >= p.nx ? 0 : x + 1;
     const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y + 1 >= p.ny ? 0 : y + 1;
     const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z + 1 >= p.nz ? 0 : z + 1;
-    auto nb = [&](int i) -> long long {
+    auto nb = [&](int i) -> I {
       const int X = cx<L>(i) == 0 ? x : (cx<L>(i) > 0 ? xp : xm);
       const int Y = cy<L>(i) == 0 ? y : (cy<L>(i) > 0 ? yp : ym);
       const int Z = cz<L>(i) == 0 ? z : (cz<L>(i) > 0 ? zp : zm);
-      return X + (long long)p.nx * (Y + (long long)p.ny * Z);
+      return X + I(p.nx) * (Y + I(p.ny) * Z);
     };
     // x - c_i = the neighbour in direction opp(i)
     T g[K][Q];
@@ -111,16 +114,16 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
     for (int k = 0; k < K; k++) {
 #pragma unroll
       for (int i = 0; i < Q; i++) {
-        const long long src = (odd && i != 0) ? (long long)(k * Q + opp<L>(i)) * N + nb(opp<L>(i))
-                                              : (long long)(k * Q + i) * N + n;
+        const I src = (odd && i != 0) ? I(k * Q + opp<L>(i)) * N + nb(opp<L>(i))
+                                              : I(k * Q + i) * N + n;
         g[k][i] = ld_s<S, T>(fin[src]);
       }
-      cs[k] = comp_state<L, T, RT>(g[k], T(rin[(long long)k * N + n]));
+      cs[k] = comp_state<L, T, RT>(g[k], T(rin[I(k) * N + n]));
     }
     auto nbr = [&](int fi, int i) -> T {
-      const long long m = nb(i);
-      if (WALLS && solid[m]) return fld[(long long)fi * N + n];
-      return fld[(long long)fi * N + m];
+      const I m = nb(i);
+      if (WALLS && solid[m]) return fld[I(fi) * N + n];
+      return fld[I(fi) * N + m];
     };
     if constexpr (MODEL == kCG) {
       T Fx[3] = {T(0), T(0), T(0)};
@@ -128,9 +131,9 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
       cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
     } else if constexpr (MODEL == kSCMR) {
       auto far = [&](int fi, int dx, int dy, int dz) -> T {
-        const long long m = wrap_index(x + dx, y + dy, z + dz, p.nx, p.ny, p.nz);
-        if (WALLS && solid[m]) return fld[(long long)fi * N + n];
-        return fld[(long long)fi * N + m];
+        const I m = (I)wrap_index(x + dx, y + dy, z + dz, p.nx, p.ny, p.nz);
+        if (WALLS && solid[m]) return fld[I(fi) * N + n];
+        return fld[I(fi) * N + m];
       };
       scmr_collide<L, T>(p, g, cs[0], cs[1], nbr, far);
     } else if constexpr (MODEL == kSCMP) {
@@ -139,22 +142,22 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
       sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
     }
 #pragma unroll
-    for (int k = 0; k < K; k++) rout[(long long)k * N + n] = RT(cs[k].q);
+    for (int k = 0; k < K; k++) rout[I(k) * N + n] = RT(cs[k].q);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      const long long d = nb(i);
+      const I d = nb(i);
       const bool bounce = WALLS && i != 0 && solid[d];
 #pragma unroll
       for (int k = 0; k < K; k++) {
         T v = g[k][i];
-        if (i != 0 && !bounce) v += p.phi[k][grp<L>(i)] * (cs[k].q - fld[(long long)(NF + k) * N + d]);
-        long long dst;
+        if (i != 0 && !bounce) v += p.phi[k][grp<L>(i)] * (cs[k].q - fld[I(NF + k) * N + d]);
+        I dst;
         if (i == 0)
-          dst = (long long)(k * Q) * N + n;
+          dst = I(k * Q) * N + n;
         else if (!inplace || odd)  // push to x + c_i; bounce-back into opp(i) of x
-          dst = bounce ? (long long)(k * Q + opp<L>(i)) * N + n : (long long)(k * Q + i) * N + d;
+          dst = bounce ? I(k * Q + opp<L>(i)) * N + n : I(k * Q + i) * N + d;
         else                       // even in-place step: back into opp(i) of x
-          dst = bounce ? (long long)(k * Q + i) * N + d : (long long)(k * Q + opp<L>(i)) * N + n;
+          dst = bounce ? I(k * Q + i) * N + d : I(k * Q + opp<L>(i)) * N + n;
         fout[dst] = st_s<S, T>(v);
       }
     }
@@ -177,7 +180,7 @@ __host__ __device__ constexpr size_t fpt_smem_bytes() {
   return (((2 * H + 1) * (NV * ne * sizeof(T) + (WALLS ? ne : 0))) + 15) & ~size_t(15);
 }
 
-template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, int H>
+template <class L, class T, class S, class RT, int MODEL, bool WALLS, bool REP, int H, class I = long long>
 __global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
     fpt_step_kernel(const S* fin, S* fout, const RT* rin, RT* rout, const T* __restrict__ fld,
                     const uint8_t* __restrict__ solid, const int* __restrict__ status,
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
   T* sf = reinterpret_cast<T*>(smem_raw);                      // [NS][NV][NE]
   uint8_t* sm = reinterpret_cast<uint8_t*>(sf + NS * NV * NE);  // [NS][NE] (walls)
   const bool inplace = mode != 0, odd = mode == 2;
-  const long long N = p.n;
+  const I N = I(p.n);
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   auto slot = [](int z) { return ((z % NS) + NS) % NS; };
   WorkRange work(blockIdx.x, p.nblk, p.ncol, p.nz, p.nchunks);
@@ -204,9 +207,9 @@ __global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
       const int gz = wrap(z, p.nz);
       for (int e = tid; e < NE; e += TX * TY) {
         const int ey = e / EX, ex = e - ey * EX;
-        const long long m = wrap(x0 - H + ex, p.nx) + (long long)p.nx * (wrap(y0 - H + ey, p.ny) + (long long)p.ny * gz);
+        const I m = wrap(x0 - H + ex, p.nx) + I(p.nx) * (wrap(y0 - H + ey, p.ny) + I(p.ny) * gz);
 #pragma unroll
-        for (int fi = 0; fi < NV; fi++) sf[(sl * NV + fi) * NE + e] = fld[(long long)fi * N + m];
+        for (int fi = 0; fi < NV; fi++) sf[(sl * NV + fi) * NE + e] = fld[I(fi) * N + m];
         if (WALLS) sm[sl * NE + e] = solid[m];
       }
     };
@@ -218,15 +221,15 @@ __global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
       const int e0 = (ty + H) * EX + (tx + H);
       const int sl0 = slot(z);
       if (x < p.nx && y < p.ny && !(WALLS && sm[sl0 * NE + e0])) {
-        const long long n = x + (long long)p.nx * (y + (long long)p.ny * z);
+        const I n = x + I(p.nx) * (y + I(p.ny) * z);
         const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x + 1 >= p.nx ? 0 : x + 1;
         const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y + 1 >= p.ny ? 0 : y + 1;
         const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z + 1 >= p.nz ? 0 : z + 1;
-        auto nb = [&](int i) -> long long {
+        auto nb = [&](int i) -> I {
           const int X = cx<L>(i) == 0 ? x : (cx<L>(i) > 0 ? xp : xm);
           const int Y = cy<L>(i) == 0 ? y : (cy<L>(i) > 0 ? yp : ym);
           const int Z = cz<L>(i) == 0 ? z : (cz<L>(i) > 0 ? zp : zm);
-          return X + (long long)p.nx * (Y + (long long)p.ny * Z);
+          return X + I(p.nx) * (Y + I(p.ny) * Z);
         };
         T g[K][Q];
         CompState<T> cs[K];
@@ -234,11 +237,11 @@ __global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
         for (int k = 0; k < K; k++) {
 #pragma unroll
           for (int i = 0; i < Q; i++) {
-            const long long src = (odd && i != 0) ? (long long)(k * Q + opp<L>(i)) * N + nb(opp<L>(i))
-                                                  : (long long)(k * Q + i) * N + n;
+            const I src = (odd && i != 0) ? I(k * Q + opp<L>(i)) * N + nb(opp<L>(i))
+                                                  : I(k * Q + i) * N + n;
             g[k][i] = ld_s<S, T>(fin[src]);
           }
-          cs[k] = comp_state<L, T, RT>(g[k], T(rin[(long long)k * N + n]));
+          cs[k] = comp_state<L, T, RT>(g[k], T(rin[I(k) * N + n]));
         }
         auto at = [&](int fi, int dx, int dy, int dz) -> T {
           const int sl = slot(z + dz), e = e0 + dy * EX + dx;
@@ -258,23 +261,23 @@ __global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
           sc2c_collide<L, T>(p, g, cs[0], cs[1], nbr);
         }
 #pragma unroll
-        for (int k = 0; k < K; k++) rout[(long long)k * N + n] = RT(cs[k].q);
+        for (int k = 0; k < K; k++) rout[I(k) * N + n] = RT(cs[k].q);
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-          const long long d = nb(i);
+          const I d = nb(i);
           const int sl = slot(z + cz<L>(i)), ed = e0 + cy<L>(i) * EX + cx<L>(i);
           const bool bounce = WALLS && i != 0 && sm[sl * NE + ed];
 #pragma unroll
           for (int k = 0; k < K; k++) {
             T v = g[k][i];
             if (i != 0 && !bounce) v += p.phi[k][grp<L>(i)] * (cs[k].q - sf[(sl * NV + NF + k) * NE + ed]);
-            long long dst;
+            I dst;
             if (i == 0)
-              dst = (long long)(k * Q) * N + n;
+              dst = I(k * Q) * N + n;
             else if (!inplace || odd)
-              dst = bounce ? (long long)(k * Q + opp<L>(i)) * N + n : (long long)(k * Q + i) * N + d;
+              dst = bounce ? I(k * Q + opp<L>(i)) * N + n : I(k * Q + i) * N + d;
             else
-              dst = bounce ? (long long)(k * Q + i) * N + d : (long long)(k * Q + opp<L>(i)) * N + n;
+              dst = bounce ? I(k * Q + i) * N + d : I(k * Q + opp<L>(i)) * N + n;
             fout[dst] = st_s<S, T>(v);
           }
         }
