@@ -193,8 +193,9 @@ lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t tx, int32_t ty, int32_t tz);
  * do not pay one launch each and fill the GPU
  * together.  The per-node arithmetic is the generic step kernel's, so a lattice's result
  * is bitwise the same alone or in any mix (it may differ by a few ulps from a lattice
- * stepped with lbm_step_* on the TMA-staged kernel).  Jobs must be initialised, periodic
- * (no walls), without the repulsion force, with two-buffer streaming (LBM_STREAM_AB), of
+ * stepped with lbm_step_* on the TMA-staged kernel).  Jobs may have walls (halfway
+ * bounce-back on their wall mask).  Jobs must be initialised, without the repulsion
+ * force, with two-buffer streaming (LBM_STREAM_AB), of
  * the batch's storage precision and on the batch's stream, with K * Q * N < 2^31 (the
  * batched kernel indexes in 32 bits).  The periodic diagnostics (diag_every) do not run inside a batch; call
  * lbm_moments per job.

@@ -26,14 +26,15 @@ struct lbm_batch {
   lbm::BatchHeader* d_hdr;
   unsigned char* d_jobs;
   lbm::BatchUnit* d_units;
-  size_t smem;
-  int grid;
+  size_t smem[2];  // [w]: kernel variant for job lists without / with wall lattices
+  int grid[2];
+  int walls;       // the current job list holds a lattice with walls
   std::vector<lbm_ctx*> ctxs;
   std::vector<int> remaining;
   std::vector<unsigned char> host_jobs;
   std::vector<lbm::BatchUnit> host_units;
   lbm::BatchHeader host_hdr;
-  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraphExec_t> graphs;  // by 2 * nsteps + walls
   unsigned long long launches;
   lbm_status sticky;
 };
@@ -65,10 +66,10 @@ cudaError_t build_graph(lbm_batch* b, int n, cudaGraphExec_t* out) {
     int sv = s;
     void* args[4] = {&hdr, &jobs, &units, &sv};
     cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void*>(b->ops->kernel);
-    kp.gridDim = dim3(b->grid, 1, 1);
+    kp.func = const_cast<void*>(b->ops->kernel[b->walls]);
+    kp.gridDim = dim3(b->grid[b->walls], 1, 1);
     kp.blockDim = dim3(lbm::kBatchTX, lbm::kBatchTY, 1);
-    kp.sharedMemBytes = (unsigned)b->smem;
+    kp.sharedMemBytes = (unsigned)b->smem[b->walls];
     kp.kernelParams = args;
     cudaGraphNode_t node;
     e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
@@ -105,21 +106,24 @@ lbm_status lbm_batch_create(int32_t precision, int32_t max_jobs, int32_t max_uni
   b->d_hdr = reinterpret_cast<lbm::BatchHeader*>(b->ws);
   b->d_jobs = b->ws + lbm::align256b(sizeof(lbm::BatchHeader));
   b->d_units = reinterpret_cast<lbm::BatchUnit*>(b->d_jobs + lbm::align256b(ops->job_bytes * size_t(max_jobs)));
-  b->smem = ops->smem_bytes();
+  b->smem[0] = ops->smem_bytes(false);
+  b->smem[1] = ops->smem_bytes(true);
+  b->walls = 0;
   b->launches = 0;
   b->sticky = LBM_OK;
   b->host_hdr = {0, 0};
-  int dev = 0, nsm = 1, per_sm = 1;
+  int dev = 0, nsm = 1, per_sm[2] = {1, 1};
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = ops->prepare(b->smem, &per_sm);
+  if (e == cudaSuccess) e = ops->prepare(false, b->smem[0], &per_sm[0]);
+  if (e == cudaSuccess) e = ops->prepare(true, b->smem[1], &per_sm[1]);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_hdr, &b->host_hdr, sizeof(lbm::BatchHeader), cudaMemcpyHostToDevice, b->stream);
   if (e != cudaSuccess) {
     delete b;
     return LBM_ECUDA;
   }
-  b->grid = std::max(1, nsm * std::max(1, per_sm));
+  for (int w = 0; w < 2; w++) b->grid[w] = std::max(1, nsm * std::max(1, per_sm[w]));
   *out = b;
   return LBM_OK;
 }
@@ -138,7 +142,7 @@ lbm_status lbm_batch_set(lbm_batch* b, lbm_ctx* const* ctxs, const int32_t* nste
     const lbm_ctx* c = ctxs[j];
     if (!c || nsteps[j] < 0) return LBM_EINVAL;
     if (c->sticky != LBM_OK || !c->initialised) return LBM_ESTATE;
-    if (c->p.precision != b->precision || c->has_walls || c->rep || c->aa || c->p.model == LBM_MODEL_SC_MR ||
+    if (c->p.precision != b->precision || c->rep || c->aa || c->p.model == LBM_MODEL_SC_MR ||
         c->stream != b->stream)
       return LBM_EINVAL;
     // the batched kernel indexes in 32 bits
@@ -146,6 +150,8 @@ lbm_status lbm_batch_set(lbm_batch* b, lbm_ctx* const* ctxs, const int32_t* nste
     nunits += units_of(c);
   }
   if (nunits > b->max_units) return LBM_EINVAL;
+  b->walls = 0;
+  for (int j = 0; j < njobs; j++) b->walls |= ctxs[j]->has_walls ? 1 : 0;
   b->ctxs.assign(ctxs, ctxs + njobs);
   b->remaining.assign(nsteps, nsteps + njobs);
   b->host_jobs.assign(b->ops->job_bytes * size_t(njobs), 0);
@@ -185,12 +191,13 @@ lbm_status lbm_batch_step(lbm_batch* b, int32_t nsteps, int32_t use_graph) {
                                   b->stream);
   if (e != cudaSuccess) return bfail(b, e);
   if (use_graph) {
-    auto it = b->graphs.find(nsteps);
+    const int key = 2 * nsteps + b->walls;
+    auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
       cudaGraphExec_t ex = nullptr;
       e = build_graph(b, nsteps, &ex);
       if (e != cudaSuccess) return bfail(b, e);
-      it = b->graphs.emplace(nsteps, ex).first;
+      it = b->graphs.emplace(key, ex).first;
     }
     e = cudaGraphLaunch(it->second, b->stream);
   } else {
@@ -200,8 +207,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int32_t nsteps, int32_t use_graph) {
       const lbm::BatchUnit* units = b->d_units;
       int sv = s;
       void* args[4] = {&hdr, &jobs, &units, &sv};
-      e = cudaLaunchKernel(b->ops->kernel, dim3(b->grid, 1, 1),
-                           dim3(lbm::kBatchTX, lbm::kBatchTY, 1), args, b->smem, b->stream);
+      e = cudaLaunchKernel(b->ops->kernel[b->walls], dim3(b->grid[b->walls], 1, 1),
+                           dim3(lbm::kBatchTX, lbm::kBatchTY, 1), args, b->smem[b->walls], b->stream);
     }
   }
   if (e != cudaSuccess) return bfail(b, e);

@@ -7,7 +7,7 @@
 // the state, the steps the job still takes).  One launch advances every job by one step:
 // a persistent grid walks the unit list with a stride, loads the unit's job descriptor
 // into shared memory and marches the unit with the same per-node code as the generic
-// step kernel (march_segment), dispatching on the job's lattice and model.  A job's result
+// step kernel (march_segment), dispatching on the job's lattice, model and wall mask.  A job's result
 // is therefore bitwise the same alone or in any mix.  Launch s of a multi-step call reads
 // the pair cur0 ^ (s & 1) and skips jobs with fewer than s + 1 steps left, so a whole call
 // can be replayed as one CUDA graph whose nodes differ only in s.
@@ -34,7 +34,9 @@ struct BatchJob {
   S* f[2];         // population buffer pair
   RT* r[2];        // reference density pair (written by the step that reads the other)
   const int* status;
+  const uint8_t* solid;  // wall mask [N] (halfway bounce-back), or nullptr
   int lattice, model;
+  int walls;       // solid != nullptr
   int cur0;        // pair holding the state when the call starts
   int nsteps;      // steps this job takes in the call
   StepParams<T> p;
@@ -56,28 +58,39 @@ size_t batch_ws_bytes(int max_jobs, int max_units) {
          align256b(sizeof(BatchUnit) * size_t(max_units));
 }
 
-template <class T, class S, class RT>
-__device__ __forceinline__ void batch_march(const BatchJob<T, S, RT>& job, const StepArrays<S, RT>& a,
-                                            const Segment& sg, unsigned char* smem) {
+template <class T, class S, class RT, bool WALLS>
+__device__ __forceinline__ void batch_march_w(const BatchJob<T, S, RT>& job, const StepArrays<S, RT>& a,
+                                              const Segment& sg, unsigned char* smem) {
   const RepParams rp{};
   if (job.lattice == LBM_D3Q19) {
     if (job.model == LBM_MODEL_CG)
-      march_segment<D3Q19, T, S, RT, kCG, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D3Q19, T, S, RT, kCG, WALLS, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else if (job.model == LBM_MODEL_SC_MP)
-      march_segment<D3Q19, T, S, RT, kSCMP, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D3Q19, T, S, RT, kSCMP, WALLS, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else
-      march_segment<D3Q19, T, S, RT, kSC2C, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D3Q19, T, S, RT, kSC2C, WALLS, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
   } else {
     if (job.model == LBM_MODEL_CG)
-      march_segment<D2Q9, T, S, RT, kCG, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D2Q9, T, S, RT, kCG, WALLS, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else if (job.model == LBM_MODEL_SC_MP)
-      march_segment<D2Q9, T, S, RT, kSCMP, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D2Q9, T, S, RT, kSCMP, WALLS, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
     else
-      march_segment<D2Q9, T, S, RT, kSC2C, false, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
+      march_segment<D2Q9, T, S, RT, kSC2C, WALLS, false, int>(a, job.p, nullptr, nullptr, rp, sg, smem);
   }
 }
 
-template <class T, class S, class RT>
+// ANYWALLS: the job list may hold lattices with walls (the kernel then carries both
+// variants of the per-node code; without wall jobs the smaller kernel runs).
+template <class T, class S, class RT, bool ANYWALLS>
+__device__ __forceinline__ void batch_march(const BatchJob<T, S, RT>& job, const StepArrays<S, RT>& a,
+                                            const Segment& sg, unsigned char* smem) {
+  if (ANYWALLS && job.walls)
+    batch_march_w<T, S, RT, ANYWALLS>(job, a, sg, smem);
+  else
+    batch_march_w<T, S, RT, false>(job, a, sg, smem);
+}
+
+template <class T, class S, class RT, bool ANYWALLS>
 __global__ void __launch_bounds__(kBatchTX * kBatchTY, min_blocks<T>())
     batch_step_kernel(const BatchHeader* __restrict__ hdr, const BatchJob<T, S, RT>* __restrict__ jobs,
                       const BatchUnit* __restrict__ units, int s) {
@@ -102,8 +115,8 @@ __global__ void __launch_bounds__(kBatchTX * kBatchTY, min_blocks<T>())
       sg.col = un.col;
       sg.z0 = (int)(((long long)un.chunk * job.p.nz) / job.p.nchunks);
       sg.z1 = (int)(((long long)(un.chunk + 1) * job.p.nz) / job.p.nchunks);
-      const StepArrays<S, RT> a{job.f[cur], job.f[cur ^ 1], job.r[cur], job.r[cur ^ 1], nullptr};
-      batch_march<T, S, RT>(job, a, sg, smem_raw);
+      const StepArrays<S, RT> a{job.f[cur], job.f[cur ^ 1], job.r[cur], job.r[cur ^ 1], job.solid};
+      batch_march<T, S, RT, ANYWALLS>(job, a, sg, smem_raw);
     }
     __syncthreads();  // the descriptor slot is rewritten for the next unit
   }
@@ -114,9 +127,10 @@ struct BatchOps {
   size_t job_bytes;                                                  // sizeof(BatchJob<...>)
   size_t (*ws_bytes)(int max_jobs, int max_units);
   void (*fill_job)(const lbm_ctx* c, int nsteps, void* dst);         // host descriptor
-  size_t (*smem_bytes)();                                            // dynamic shared memory
-  cudaError_t (*prepare)(size_t smem, int* blocks_per_sm);           // opt-in + occupancy
-  const void* kernel;                                                // batch_step_kernel<...>
+  // [w]: the kernel for job lists without (w = 0) or with (w = 1) lattices with walls
+  size_t (*smem_bytes)(bool walls);                                  // dynamic shared memory
+  cudaError_t (*prepare)(bool walls, size_t smem, int* blocks_per_sm);  // opt-in + occupancy
+  const void* kernel[2];                                             // batch_step_kernel<...>
 };
 const BatchOps* batch_ops(int precision);  // nullptr when the precision has no batch kernel
 
@@ -128,6 +142,8 @@ void batch_fill_job(const lbm_ctx* c, int nsteps, void* dst) {
   j.r[0] = static_cast<RT*>(c->r[0]);
   j.r[1] = static_cast<RT*>(c->r[1]);
   j.status = &c->diag->status;
+  j.solid = c->has_walls ? c->solid : nullptr;
+  j.walls = c->has_walls ? 1 : 0;
   j.lattice = c->p.lattice;
   j.model = c->p.model;
   j.cur0 = c->cur;
@@ -141,7 +157,7 @@ void batch_fill_job(const lbm_ctx* c, int nsteps, void* dst) {
 }
 
 template <class T, class S, class RT>
-size_t batch_smem_bytes() {
+size_t batch_smem_bytes(bool walls) {
   size_t m = 0;
   m = std::max(m, step_smem_bytes<D3Q19, T, kCG, false>(kBatchTX, kBatchTY));
   m = std::max(m, step_smem_bytes<D3Q19, T, kSCMP, false>(kBatchTX, kBatchTY));
@@ -149,12 +165,20 @@ size_t batch_smem_bytes() {
   m = std::max(m, step_smem_bytes<D2Q9, T, kCG, false>(kBatchTX, kBatchTY));
   m = std::max(m, step_smem_bytes<D2Q9, T, kSCMP, false>(kBatchTX, kBatchTY));
   m = std::max(m, step_smem_bytes<D2Q9, T, kSC2C, false>(kBatchTX, kBatchTY));
+  if (walls) {
+    m = std::max(m, step_smem_bytes<D3Q19, T, kCG, true>(kBatchTX, kBatchTY));
+    m = std::max(m, step_smem_bytes<D3Q19, T, kSCMP, true>(kBatchTX, kBatchTY));
+    m = std::max(m, step_smem_bytes<D3Q19, T, kSC2C, true>(kBatchTX, kBatchTY));
+    m = std::max(m, step_smem_bytes<D2Q9, T, kCG, true>(kBatchTX, kBatchTY));
+    m = std::max(m, step_smem_bytes<D2Q9, T, kSCMP, true>(kBatchTX, kBatchTY));
+    m = std::max(m, step_smem_bytes<D2Q9, T, kSC2C, true>(kBatchTX, kBatchTY));
+  }
   return m;
 }
 
 template <class T, class S, class RT>
-cudaError_t batch_prepare(size_t smem, int* blocks_per_sm) {
-  auto k = batch_step_kernel<T, S, RT>;
+cudaError_t batch_prepare(bool walls, size_t smem, int* blocks_per_sm) {
+  auto k = walls ? batch_step_kernel<T, S, RT, true> : batch_step_kernel<T, S, RT, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBatchTX * kBatchTY, smem);
@@ -162,9 +186,13 @@ cudaError_t batch_prepare(size_t smem, int* blocks_per_sm) {
 
 template <class T, class S, class RT>
 const BatchOps* make_batch_ops() {
-  static const BatchOps ops = {sizeof(BatchJob<T, S, RT>), &batch_ws_bytes<T, S, RT>, &batch_fill_job<T, S, RT>,
-                               &batch_smem_bytes<T, S, RT>, &batch_prepare<T, S, RT>,
-                               reinterpret_cast<const void*>(&batch_step_kernel<T, S, RT>)};
+  static const BatchOps ops = {sizeof(BatchJob<T, S, RT>),
+                               &batch_ws_bytes<T, S, RT>,
+                               &batch_fill_job<T, S, RT>,
+                               &batch_smem_bytes<T, S, RT>,
+                               &batch_prepare<T, S, RT>,
+                               {reinterpret_cast<const void*>(&batch_step_kernel<T, S, RT, false>),
+                                reinterpret_cast<const void*>(&batch_step_kernel<T, S, RT, true>)}};
   return &ops;
 }
 
