@@ -1,4 +1,4 @@
-"""z-slab domain decomposition (decomp.py) on one GPU: two sub-domains of the same lattice,
+"""z-slab domain decomposition (decomp.py) on one GPU: two or three sub-domains of a lattice,
 each an extended slab stepped by the library's own kernels, their ghost planes moved with
 lbm_get_state_planes / lbm_set_state_planes (device copies); after every step the owned
 planes equal the single-domain run's raw state bit for bit.  (The kernels compute every
@@ -24,11 +24,13 @@ CASES = {
     "cg_fp16_ring": (lambda: C.cg_drop3d(nx=64, ny=32, nz=30), 2, (32, 16, 0)),    # ring kernel, 16-bit
     "cg_rep_fp64": (C.cg_rep3d, 0, (32, 8, 16)),                                   # repulsion, H = 3
     "cg_walls_fp32": (C.cg_walls3d, 1, (32, 8, 16)),                               # walls, body force
+    "sc_mr_fp32": (lambda: C.sc_mr3d(nx=20, ny=16, nz=24), 1, (32, 8, 0)),          # multirange, H = 3
+    "sc_mr_walls_fp64": (lambda: C.sc_mr3d(nz=18, walls=True), 0, (32, 8, 0)),      # multirange with walls
 }
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_two_slabs_on_one_gpu_match_single_domain(lbm, name):
+@pytest.mark.parametrize("name,world", [(n, 2) for n in CASES] + [("cg_fp32_cluster", 3), ("sc_mr_fp32", 3)])
+def test_slabs_on_one_gpu_match_single_domain(lbm, name, world):
     from paper_2110_05197_gb300 import decomp
     make, precision, tiling = CASES[name]
     case = make()
@@ -38,7 +40,6 @@ def test_two_slabs_on_one_gpu_match_single_domain(lbm, name):
     full = C.gpu_lattice(lbm, case, precision)
     full.set_tiling(*tiling)
     full.step(steps)
-    world = 2
     H = decomp.ghost_planes(kw["model"], kw.get("rep_pi", 0.0))
     doms = [decomp.lattice_slab(params, decomp.Slab(kw["nz"], world, r, H), case.rho_r, case.rho_b, case.u,
                                 case.solid) for r in range(world)]
