@@ -176,6 +176,8 @@ RING_CASES = {
     "cg_ring96": lambda: cg_drop3d(nx=96, ny=16, nz=7, ratio=3.0),         # 32 x 16: 3
     "cg_ring_body": lambda: cg_drop3d(nx=32, ny=16, nz=9, body_force=(1e-5, 0.0, 2e-6)),
     "sc_ring64": lambda: sc_mp3d(nx=64, ny=16, nz=14),                     # 32 x 16: 2; 64 x 8: 1
+    "cg_ring256": lambda: cg_drop3d(nx=256, ny=16, nz=6),                  # 32 x 16: 8 (the largest cluster)
+    "sc_ring512": lambda: sc_mp3d(nx=512, ny=16, nz=14),                   # 64 x 8 and 64 x 4: 8
 }
 
 

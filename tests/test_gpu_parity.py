@@ -146,12 +146,12 @@ def test_16bit_storage_accuracy(orc, lbm, name, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
-@pytest.mark.parametrize("shape", [(37, 21, 19), (64, 24, 20), (96, 64, 48), (288, 16, 6)])
+@pytest.mark.parametrize("shape", [(37, 21, 19), (64, 24, 20), (96, 64, 48), (256, 16, 6), (288, 16, 6)])
 def test_tiling_does_not_change_results(lbm, precision, shape):
     """Within one kernel the launch shape never changes a bit: the generic kernel in several
     tilings, and the TMA-staged kernel (32 x 8 tiles, used for the x % 32 == 0 shapes in
-    FP32/FP16; with the x-halo exchanged in a cluster of nx / 32 blocks up to nx = 256, with
-    fetched halo columns at nx = 288) for two z-chunk lengths, each also as a persistent
+    FP32/FP16; with the x-halo exchanged in a cluster of nx / 32 blocks up to nx = 256 --
+    the largest cluster, 8 blocks --, with fetched halo columns at nx = 288) for two z-chunk lengths, each also as a persistent
     grid (tz = 0; at 96 x 64 x 48 every block's share spans several columns).  Up to
     nx = 256 the cluster kernel also runs 32 x 4 tiles (two blocks per SM), which must give
     the same bits as its 32 x 8 tiles, and, where nx % 64 == 0, 64 x 4 tiles in clusters of
