@@ -58,8 +58,12 @@ cudaError_t launch_rep_prepass_t(lbm_ctx* c, int buf) {
   colour_kernel<L, T, S, RT><<<grid, 256, 0, c->stream>>>(static_cast<const S*>(c->f[buf]),
                                                            static_cast<const RT*>(c->r[buf]),
                                                            static_cast<T*>(c->colour), a, c->aa ? (buf & 1) : 0);
-  normals_kernel<L, T><<<grid, 256, 0, c->stream>>>(static_cast<const T*>(c->colour),
-                                                    c->has_walls ? c->solid : nullptr, static_cast<T*>(c->normals), a);
+  if (3 * c->N < (1LL << 31))  // 32-bit indices: the normals array holds 3 N values
+    normals_kernel<L, T, int><<<grid, 256, 0, c->stream>>>(
+        static_cast<const T*>(c->colour), c->has_walls ? c->solid : nullptr, static_cast<T*>(c->normals), a);
+  else
+    normals_kernel<L, T, long long><<<grid, 256, 0, c->stream>>>(
+        static_cast<const T*>(c->colour), c->has_walls ? c->solid : nullptr, static_cast<T*>(c->normals), a);
   c->launches += 2;
   return cudaGetLastError();
 }

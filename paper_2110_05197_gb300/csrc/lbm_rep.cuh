@@ -39,19 +39,28 @@ __device__ __forceinline__ long long wrap_index(int x, int y, int z, int nx, int
   z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
   return x + (long long)nx * (y + (long long)ny * z);
 }
+// The same in index type I (int when every node index of the lattice fits 32 bits).
+template <class I>
+__device__ __forceinline__ I wrap_index_t(int x, int y, int z, int nx, int ny, int nz) {
+  x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+  z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+  return x + I(nx) * (y + I(ny) * z);
+}
 
 // normals[3][N] (zero where undefined)
-template <class L, class T>
+template <class L, class T, class I = long long>
 __global__ void normals_kernel(const T* __restrict__ colour, const uint8_t* __restrict__ solid,
                                T* __restrict__ normals, RepParams a) {
-  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+  const I N = I(a.n);
+  for (I m = blockIdx.x * I(blockDim.x) + threadIdx.x; m < N; m += I(gridDim.x) * blockDim.x) {
     int x, y, z;
     node_coords(m, a.nx, a.ny, a.n, x, y, z);
     T g[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int q = 0; q < L::NP; q++) {
-      const long long mp = wrap_index(x + L::pcx(q), y + L::pcy(q), z + L::pcz(q), a.nx, a.ny, a.nz);
-      const long long mm = wrap_index(x - L::pcx(q), y - L::pcy(q), z - L::pcz(q), a.nx, a.ny, a.nz);
+      const I mp = wrap_index_t<I>(x + L::pcx(q), y + L::pcy(q), z + L::pcz(q), a.nx, a.ny, a.nz);
+      const I mm = wrap_index_t<I>(x - L::pcx(q), y - L::pcy(q), z - L::pcz(q), a.nx, a.ny, a.nz);
       const T vp = (solid && solid[mp]) ? colour[m] : colour[mp];
       const T vm = (solid && solid[mm]) ? colour[m] : colour[mm];
       const T d = T(3.0 * L::w(L::pgrp(q))) * (vp - vm);
@@ -61,25 +70,27 @@ __global__ void normals_kernel(const T* __restrict__ colour, const uint8_t* __re
     }
     const T gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     const bool ok = gn > T(a.grad_eps) && !(solid && solid[m]);
-    for (int d = 0; d < 3; d++) normals[(long long)d * a.n + m] = ok ? g[d] / gn : T(0);
+    for (int d = 0; d < 3; d++) normals[I(d) * N + m] = ok ? g[d] / gn : T(0);
   }
 }
 
-// F_rep at node (x, y, z) from the normal and colour fields (Eq. repForce).
-template <class L, class T>
+// F_rep at node (x, y, z) from the normal and colour fields (Eq. repForce); I: the
+// caller's index type.
+template <class L, class T, class I = long long>
 __device__ __forceinline__ void rep_force(const T* __restrict__ normals, const T* __restrict__ colour,
                                           const uint8_t* __restrict__ solid, int x, int y, int z, const RepParams& a,
                                           T (&F)[3]) {
   F[0] = F[1] = F[2] = T(0);
-  const long long m = x + (long long)a.nx * (y + (long long)a.ny * z);
-  const T n0 = normals[m], n1 = normals[a.n + m], n2 = normals[2 * a.n + m];
+  const I N = I(a.n);
+  const I m = x + I(a.nx) * (y + I(a.ny) * z);
+  const T n0 = normals[m], n1 = normals[N + m], n2 = normals[2 * N + m];
   if (n0 == T(0) && n1 == T(0) && n2 == T(0)) return;  // no normal at x
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int i = 1; i < L::Q; i++) {
-    const long long mm = wrap_index(x + cx<L>(i), y + cy<L>(i), z + cz<L>(i), a.nx, a.ny, a.nz);
+    const I mm = wrap_index_t<I>(x + cx<L>(i), y + cy<L>(i), z + cz<L>(i), a.nx, a.ny, a.nz);
     if (solid && solid[mm]) continue;
-    const T p0 = normals[mm], p1 = normals[a.n + mm], p2 = normals[2 * a.n + mm];
+    const T p0 = normals[mm], p1 = normals[N + mm], p2 = normals[2 * N + mm];
     const T nc = cx<L>(i) * n0 + cy<L>(i) * n1 + cz<L>(i) * n2;
     const T pc = cx<L>(i) * p0 + cy<L>(i) * p1 + cz<L>(i) * p2;
     if (-(nc * pc) > T(0)) {  // H(0) = 0; an undefined neighbour normal gives pc = 0

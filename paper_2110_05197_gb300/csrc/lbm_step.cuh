@@ -650,7 +650,7 @@ __device__ __forceinline__ void march_segment(const StepArrays<S, RT>& a, const 
     };
     if constexpr (MODEL == kCG) {
       T Fx[3] = {T(0), T(0), T(0)};
-      if constexpr (REP) rep_force<L, T>(normals, colour, WALLS ? solid : nullptr, gx, gy, z, rp, Fx);
+      if constexpr (REP) rep_force<L, T, I>(normals, colour, WALLS ? solid : nullptr, gx, gy, z, rp, Fx);
       cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
     } else if constexpr (MODEL == kSCMP) {
       scmp_collide<L, T>(p, g, cs[0], nbr);

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256, min_blocks<T>())
     };
     if constexpr (MODEL == kCG) {
       T Fx[3] = {T(0), T(0), T(0)};
-      if constexpr (REP) rep_force<L, T>(normals, colour, WALLS ? solid : nullptr, x, y, z, rp, Fx);
+      if constexpr (REP) rep_force<L, T, I>(normals, colour, WALLS ? solid : nullptr, x, y, z, rp, Fx);
       cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
     } else if constexpr (MODEL == kSCMR) {
       auto far = [&](int fi, int dx, int dy, int dz) -> T {
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kFpTX * kFpTY, min_blocks<T>())
         auto nbr = [&](int fi, int i) -> T { return at(fi, cx<L>(i), cy<L>(i), cz<L>(i)); };
         if constexpr (MODEL == kCG) {
           T Fx[3] = {T(0), T(0), T(0)};
-          if constexpr (REP) rep_force<L, T>(normals, colour, WALLS ? solid : nullptr, x, y, z, rp, Fx);
+          if constexpr (REP) rep_force<L, T, I>(normals, colour, WALLS ? solid : nullptr, x, y, z, rp, Fx);
           cg_collide<L, T>(p, g, cs[0], cs[1], nbr, Fx);
         } else if constexpr (MODEL == kSCMR) {
           scmr_collide<L, T>(p, g, cs[0], cs[1], nbr, at);
