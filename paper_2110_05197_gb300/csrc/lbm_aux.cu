@@ -28,14 +28,16 @@ __device__ __forceinline__ __half from_d<__half>(double v) { return __float2half
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
-__device__ __forceinline__ long long nb_index(int x, int y, int z, int dx, int dy, int dz, int nx, int ny, int nz) {
+// Index of the periodic neighbour (x + dx, y + dy, z + dz) in index type I.
+template <class I>
+__device__ __forceinline__ I nb_index_t(int x, int y, int z, int dx, int dy, int dz, int nx, int ny, int nz) {
   x += dx;
   y += dy;
   z += dz;
   x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
   y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
   z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-  return x + (long long)nx * (y + (long long)ny * z);
+  return x + I(nx) * (y + I(ny) * z);
 }
 
 struct AuxParams {
@@ -119,14 +121,14 @@ __device__ __forceinline__ void node_xyz(long long n, const AuxParams& a, int& x
 }
 
 // 3 sum_i w_i phi(x + c_i) c_i with a wall neighbour replaced by the centre value.
-template <class L, class C, class E>
-__device__ void grad_c(const E* phi, const uint8_t* solid, long long n, int x, int y, int z,
-                       const AuxParams& a, C g[3]) {
+template <class L, class C, class E, class I>
+__device__ void grad_c(const E* phi, const uint8_t* solid, I n, int x, int y, int z, const AuxParams& a, C g[3]) {
   g[0] = g[1] = g[2] = C(0);
+#pragma unroll
   for (int q = 0; q < L::NP; q++) {
     const int i = 2 * q + 1;
-    const long long mp = nb_index(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
-    const long long mm = nb_index(x, y, z, -cx<L>(i), -cy<L>(i), -cz<L>(i), a.nx, a.ny, a.nz);
+    const I mp = nb_index_t<I>(x, y, z, cx<L>(i), cy<L>(i), cz<L>(i), a.nx, a.ny, a.nz);
+    const I mm = nb_index_t<I>(x, y, z, -cx<L>(i), -cy<L>(i), -cz<L>(i), a.nx, a.ny, a.nz);
     const C vp = C((solid && solid[mp]) ? phi[n] : phi[mp]);
     const C vm = C((solid && solid[mm]) ? phi[n] : phi[mm]);
     const C d = C(3.0 * L::w(L::pgrp(q))) * (vp - vm);
@@ -163,21 +165,22 @@ __global__ void to_compute_kernel(const double* __restrict__ rr, const double* _
   }
 }
 
-template <class L, class S, class RT>
+template <class L, class S, class RT, class I>
 __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __restrict__ ra, RT* __restrict__ rb_,
                                const double* __restrict__ rr, const double* __restrict__ rb,
                                const double* __restrict__ U, const uint8_t* __restrict__ solid,
                                const step_t<S>* __restrict__ fc, AuxParams a) {
   using C = step_t<S>;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.n; n += (long long)gridDim.x * blockDim.x) {
+  const I N = I(a.n);
+  for (I n = blockIdx.x * I(blockDim.x) + threadIdx.x; n < N; n += I(gridDim.x) * blockDim.x) {
     C out[L::Q];
     if (solid && solid[n]) {
       for (int k = 0; k < a.K; k++) {
-        ra[(long long)k * a.n + n] = RT(0);
-        if (rb_) rb_[(long long)k * a.n + n] = RT(0);
+        ra[I(k) * N + n] = RT(0);
+        if (rb_) rb_[I(k) * N + n] = RT(0);
         for (int i = 0; i < L::Q; i++) {
-          fa[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(0.0);
-          if (fb) fb[(long long)(k * L::Q + i) * a.n + n] = from_d<S>(0.0);
+          fa[I(k * L::Q + i) * N + n] = from_d<S>(0.0);
+          if (fb) fb[I(k * L::Q + i) * N + n] = from_d<S>(0.0);
         }
       }
       continue;
@@ -187,12 +190,12 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
     C u[3] = {C(0), C(0), C(0)};
     if (U) {
       u[0] = C(U[n]);
-      u[1] = C(U[a.n + n]);
-      u[2] = C(U[2 * a.n + n]);
+      u[1] = C(U[N + n]);
+      u[2] = C(U[2 * N + n]);
     }
     C en = C(0);
     if (a.model == LBM_MODEL_CG && a.enhanced) {
-      const C r = fc ? fc[n] : C(rr[n]), b = fc ? fc[a.n + n] : C(rb[n]), rho = r + b;
+      const C r = fc ? fc[n] : C(rr[n]), b = fc ? fc[N + n] : C(rb[n]), rho = r + b;
       en = C(1) / ((r / rho) / C(a.nu_r) + (b / rho) / C(a.nu_b));  // Eq. interpVisc
     }
     // Only pair 0 is written for fluid nodes: the first step writes every population and
@@ -203,14 +206,14 @@ __global__ void init_eq_kernel(S* __restrict__ fa, S* __restrict__ fb, RT* __res
       C g[3] = {C(0), C(0), C(0)};
       if (a.model == LBM_MODEL_CG) {
         if (fc)
-          grad_c<L, C>(fc + (long long)k * a.n, solid, n, x, y, z, a, g);
+          grad_c<L, C>(fc + I(k) * N, solid, n, x, y, z, a, g);
         else
           grad_c<L, C>(phi, solid, n, x, y, z, a, g);
       }
       feq_dev<L, C>(C(phi[n]), a.phi[k], en, u, g, C(phi[n] - (double)rref), out);
-      ra[(long long)k * a.n + n] = rref;
+      ra[I(k) * N + n] = rref;
       for (int i = 0; i < L::Q; i++) {
-        fa[(long long)(k * L::Q + i) * a.n + n] = st_s<S, C>(out[i]);
+        fa[I(k * L::Q + i) * N + n] = st_s<S, C>(out[i]);
       }
     }
   }
@@ -275,7 +278,7 @@ __global__ void aa_gather_kernel(const S* __restrict__ f, S* __restrict__ out, c
 // j = sum_k sum_i c_i f^k_i into jm [3][N] (FP64), and for the multirange model the
 // pseudopotentials Psi_s of both species in the step's compute type into mrpsi [2][N]
 // (read 92 times per node by the diagnostics' belt sums).
-template <class L, class S, class RT>
+template <class L, class S, class RT, class I>
 __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__ f1, const RT* __restrict__ r0,
                                  const RT* __restrict__ r1, const lbm_diag* __restrict__ d, int cur,
                                  double* __restrict__ rr, double* __restrict__ rb, double* __restrict__ psi,
@@ -285,7 +288,8 @@ __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__
   const S* f = b ? f1 : f0;
   const RT* r = b ? r1 : r0;
   const bool odd = a.aa && (b & 1);
-  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.n; m += (long long)gridDim.x * blockDim.x) {
+  const I N = I(a.n);
+  for (I m = blockIdx.x * I(blockDim.x) + threadIdx.x; m < N; m += I(gridDim.x) * blockDim.x) {
     // momentum summed exactly (ExactSum): the colours' momenta nearly cancel at
     // interfaces, so rounding in the sum would show up in the reported u; the shift
     // phi_i r is symmetric in c_i and carries no momentum: opposite pairs of the stored
@@ -294,15 +298,15 @@ __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__
     for (int k = 0; k < 2; k++) {
       double s = 0.0;
       if (k < a.K) {
-        ExactSum<C> acc{static_cast<C>(r[(long long)k * a.n + m])};  // sum_i phi_i = 1
+        ExactSum<C> acc{static_cast<C>(r[I(k) * N + m])};  // sum_i phi_i = 1
 #pragma unroll
         for (int i = 0; i < L::Q; i++)
-          acc.add(ld_s<S, C>(f[aa_index_n<L>(k, i, m, a.nx, a.ny, a.nz, a.n, odd)]));
+          acc.add(ld_s<S, C>(f[aa_index_nt<L, I>(k, i, m, a.nx, a.ny, a.nz, N, odd)]));
         s = acc.value();
 #pragma unroll
         for (int q = 0; q < L::NP; q++) {
-          const C vp = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 1, m, a.nx, a.ny, a.nz, a.n, odd)]);
-          const C vm = ld_s<S, C>(f[aa_index_n<L>(k, 2 * q + 2, m, a.nx, a.ny, a.nz, a.n, odd)]);
+          const C vp = ld_s<S, C>(f[aa_index_nt<L, I>(k, 2 * q + 1, m, a.nx, a.ny, a.nz, N, odd)]);
+          const C vm = ld_s<S, C>(f[aa_index_nt<L, I>(k, 2 * q + 2, m, a.nx, a.ny, a.nz, N, odd)]);
           if (L::pcx(q)) { jx.add(L::pcx(q) > 0 ? vp : -vp); jx.add(L::pcx(q) > 0 ? -vm : vm); }
           if (L::pcy(q)) { jy.add(L::pcy(q) > 0 ? vp : -vp); jy.add(L::pcy(q) > 0 ? -vm : vm); }
           if (L::pcz(q)) { jz.add(L::pcz(q) > 0 ? vp : -vp); jz.add(L::pcz(q) > 0 ? -vm : vm); }
@@ -313,12 +317,12 @@ __global__ void densities_kernel(const S* __restrict__ f0, const S* __restrict__
       if (k == 0 && a.model == LBM_MODEL_SC_MP) psi[m] = a.rho0 * (1.0 - exp(-s / a.rho0));
       if (mrpsi) {  // Psi_s = rho_0 (1 - exp(-rho_s / rho_0)) in the compute type
         const C c0 = C(a.rho0), ic0 = C(1.0 / a.rho0);
-        mrpsi[(long long)k * a.n + m] = c0 * (C(1) - exp(-C(s) * ic0));
+        mrpsi[I(k) * N + m] = c0 * (C(1) - exp(-C(s) * ic0));
       }
     }
     jm[m] = jx.value();
-    jm[a.n + m] = jy.value();
-    jm[2 * a.n + m] = jz.value();
+    jm[N + m] = jy.value();
+    jm[2 * N + m] = jz.value();
   }
 }
 
@@ -569,7 +573,10 @@ cudaError_t init_t(lbm_ctx* c, const double* rr, const double* rb, const double*
     c->launches += 1;
   }
   // in-place streaming: one buffer pair (the second pointers alias the first)
-  init_eq_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
+  // 32-bit indices where every index (populations K Q N, velocity 3 N) fits
+  auto kern = (long long)c->K * c->Q * c->N < (1LL << 31) ? init_eq_kernel<L, S, RT, int>
+                                                          : init_eq_kernel<L, S, RT, long long>;
+  kern<<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(
       static_cast<S*>(c->f[0]), c->aa ? nullptr : static_cast<S*>(c->f[1]), static_cast<RT*>(c->r[0]),
       c->aa ? nullptr : static_cast<RT*>(c->r[1]), rr, rb, u, c->has_walls ? c->solid : nullptr, fc, a);
   return cudaGetLastError();
@@ -616,8 +623,9 @@ cudaError_t diag_t(lbm_ctx* c, double* uo) {
   double* jm = c->stage + 2 * c->N;   // momentum, then (if requested here) the velocity
   double* psi = c->stage + 5 * c->N;  // SC multiphase psi (FP64), or the multirange Psi_s
   step_t<S>* mrpsi = c->p.model == LBM_MODEL_SC_MR ? reinterpret_cast<step_t<S>*>(psi) : nullptr;
-  densities_kernel<L, S, RT><<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(f0, f1, r0, r1, c->diag, c->cur, rr,
-                                                                               rb, psi, jm, mrpsi, a);
+  auto dens = (long long)c->K * c->Q * c->N < (1LL << 31) ? densities_kernel<L, S, RT, int>
+                                                          : densities_kernel<L, S, RT, long long>;
+  dens<<<grid_for(c->N, 256, 8192), 256, 0, c->stream>>>(f0, f1, r0, r1, c->diag, c->cur, rr, rb, psi, jm, mrpsi, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (c->rep) {

@@ -40,6 +40,19 @@ __device__ __forceinline__ long long aa_index(int k, int i, long long n, int x, 
   return (long long)(k * L::Q + opp<L>(i)) * N + wrap_index(x - cx<L>(i), y - cy<L>(i), z - cz<L>(i), nx, ny, nz);
 }
 
+// The same in index type I (int when K Q N < 2^31).
+template <class L, class I>
+__device__ __forceinline__ I aa_index_nt(int k, int i, I n, int nx, int ny, int nz, I N, bool odd) {
+  if (!odd || i == 0) return I(k * L::Q + i) * N + n;
+  int x, y, z;
+  node_coords(n, nx, ny, N, x, y, z);
+  const int X = x - cx<L>(i), Y = y - cy<L>(i), Z = z - cz<L>(i);
+  const int Xw = X < 0 ? X + nx : (X >= nx ? X - nx : X);
+  const int Yw = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
+  const int Zw = Z < 0 ? Z + nz : (Z >= nz ? Z - nz : Z);
+  return I(k * L::Q + opp<L>(i)) * N + (Xw + I(nx) * (Yw + I(ny) * Zw));
+}
+
 template <class L>
 __device__ __forceinline__ long long aa_index_n(int k, int i, long long n, int nx, int ny, int nz, long long N,
                                                 bool odd) {
