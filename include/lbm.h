@@ -57,7 +57,9 @@ typedef enum {
   LBM_EUNSTABLE = 4,  /* the blow-up check tripped: non-finite, negative density or |u| too large */
   LBM_ESTATE = 5,     /* call does not fit the context: wrong model for this step call, or
                          stepping before lbm_init_fields */
-  LBM_ETIMEOUT = 6    /* a bounded device wait gave up (reserved for the batched engine) */
+  LBM_ETIMEOUT = 6    /* a step kernel's bounded device wait gave up (2 s of GPU time on one
+                         wait) or its shared-memory layout check failed; the state stops
+                         advancing and lbm_moments(totals) reports this status */
 } lbm_status;
 
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
